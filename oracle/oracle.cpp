@@ -1,0 +1,289 @@
+// CPU oracle for triangle listing with a given vertex ordering
+// (Lecuyer, Jachiet, Magnien, Tabourier, arXiv:2203.04774).
+//
+// TEST INFRASTRUCTURE ONLY.  This file is a plain, slow, obviously correct
+// restatement of the paper, used to check the CUDA path.  Only the test
+// suite, the smoke check of __graft_entry__ and the CPU-baseline leg of
+// bench.py may load it.  It shares no code, header or constant with the
+// CUDA library: the hash below is written out again from its definition.
+//
+// Every function cites the passage it follows:
+//   * graph model, ordering, DAG G_pi, N+ / N-, d+ / d-   : Sec. 1.3
+//   * cleaning (loops removed, directions merged)         : Sec. 4.1
+//   * Algorithm 1 (A++, "L+n") and Algorithm 2 (A+-, "S1+n"): Sec. 2.1
+//   * Property 1 (operation counts)                       : Sec. 2.1
+//   * cost C++ and C+- (Definition, "Cost induced by an ordering"): Sec. 3.1
+//   * mere-listing task (ordering given)                  : Sec. 3.2
+//
+// Readings where the paper leaves a choice open:
+//   * rank[v] = pi_v - 1 (0-based) instead of the 1-based pi of Sec. 1.3.
+//   * A triangle is reported as its three ORIGINAL vertex ids sorted
+//     a < b < c; the set of triangles is unique, their order is not.
+//   * "probes" counts executions of the test "if B[v]" (Algorithm 1) or
+//     "if B[w]" (Algorithm 2); Property 1 says this equals C++ resp. C+-.
+//     The m set and m reset operations on B are counted separately.
+//   * Set hash of a triangle set (not in the paper; an order-independent
+//     checksum for large outputs):  H = sum over triangles of
+//     h(a,b,c) = mix(mix(mix(a + G) + b + G) + c + G)  (mod 2^64), where
+//     G = 0x9e3779b97f4a7c15 and mix is the splitmix64 finaliser (Steele,
+//     Lea and Flood, OOPSLA 2014).
+//
+// Plain C++17 and the standard library only.
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <utility>
+#include <vector>
+
+namespace {
+
+constexpr uint64_t kGolden = 0x9e3779b97f4a7c15ULL;
+
+uint64_t mix(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+
+uint64_t triple_hash(uint32_t a, uint32_t b, uint32_t c) {
+  uint64_t t = mix(uint64_t(a) + kGolden);
+  t = mix(t + uint64_t(b) + kGolden);
+  return mix(t + uint64_t(c) + kGolden);
+}
+
+struct Graph {
+  uint32_t n = 0;
+  // Undirected simple edge set E as pairs (a, b), a < b, original ids.
+  std::vector<std::pair<uint32_t, uint32_t>> E;
+  // Ordering and the DAG G_pi in rank space (Sec. 1.3).
+  std::vector<uint32_t> rank;  // rank[v] = pi_v - 1
+  std::vector<uint32_t> inv;   // inv[rank[v]] = v
+  std::vector<std::vector<uint32_t>> out;  // N+_x: successors of rank x, ascending
+  std::vector<std::vector<uint32_t>> in;   // N-_x: predecessors of rank x, ascending
+};
+
+// Where found triangles go: a buffer of triples (may be absent), a count and
+// the set hash.
+struct Sink {
+  uint32_t *buf = nullptr;
+  uint64_t cap = 0;
+  uint64_t count = 0;
+  uint64_t hash = 0;
+  const Graph *g = nullptr;
+
+  // Report triangle {u, v, w} given in rank space.
+  void output(uint32_t u, uint32_t v, uint32_t w) {
+    uint32_t t[3] = {g->inv[u], g->inv[v], g->inv[w]};
+    std::sort(t, t + 3);
+    if (buf && count < cap) {
+      buf[3 * count + 0] = t[0];
+      buf[3 * count + 1] = t[1];
+      buf[3 * count + 2] = t[2];
+    }
+    ++count;
+    hash += triple_hash(t[0], t[1], t[2]);
+  }
+};
+
+// Orient every edge of E by the ordering (Sec. 1.3): (u, v) in E_pi iff
+// pi_u < pi_v, stored as u -> v in rank space.
+void build_dag(Graph &g) {
+  g.out.assign(g.n, {});
+  g.in.assign(g.n, {});
+  for (const auto &e : g.E) {
+    uint32_t ra = g.rank[e.first], rb = g.rank[e.second];
+    uint32_t lo = std::min(ra, rb), hi = std::max(ra, rb);
+    g.out[lo].push_back(hi);
+    g.in[hi].push_back(lo);
+  }
+  for (auto &l : g.out) std::sort(l.begin(), l.end());
+  for (auto &l : g.in) std::sort(l.begin(), l.end());
+}
+
+// Algorithm 1 (A++), literally: for each vertex w, mark N-_w in B; for every
+// u in N-_w and every v in N+_u, a set B[v] reports {u, v, w}; reset B.
+// The outer loop runs over ranks [w_begin, w_end).
+void list_app_literal(const Graph &g, uint32_t w_begin, uint32_t w_end, Sink &s,
+                      uint64_t &probes) {
+  std::vector<char> B(g.n, 0);
+  for (uint32_t w = w_begin; w < w_end; ++w) {
+    for (uint32_t v : g.in[w]) B[v] = 1;
+    for (uint32_t u : g.in[w]) {
+      for (uint32_t v : g.out[u]) {
+        ++probes;
+        if (B[v]) s.output(u, v, w);
+      }
+    }
+    for (uint32_t v : g.in[w]) B[v] = 0;
+  }
+}
+
+// Algorithm 2 (A+-), literally: for each vertex u, mark N+_u in B; for every
+// v in N+_u and every w in N+_v, a set B[w] reports {u, v, w}; reset B.
+void list_apm_literal(const Graph &g, uint32_t u_begin, uint32_t u_end, Sink &s,
+                      uint64_t &probes) {
+  std::vector<char> B(g.n, 0);
+  for (uint32_t u = u_begin; u < u_end; ++u) {
+    for (uint32_t w : g.out[u]) B[w] = 1;
+    for (uint32_t v : g.out[u]) {
+      for (uint32_t w : g.out[v]) {
+        ++probes;
+        if (B[w]) s.output(u, v, w);
+      }
+    }
+    for (uint32_t w : g.out[u]) B[w] = 0;
+  }
+}
+
+// The same two algorithms written as one sorted-list intersection per seed
+// edge (Sec. 2.1, "neighborhood intersection"): A++ seeds on the long edge
+// L = (u, w) and intersects N+_u with N-_w; A+- seeds on the first short edge
+// S1 = (u, v) and intersects N+_u with N+_v.  std::set_intersection does the
+// work; "probes" here counts the scanned list (N+_u resp. N+_v) so that it is
+// comparable with the literal form.
+void list_app_sets(const Graph &g, uint32_t w_begin, uint32_t w_end, Sink &s,
+                   uint64_t &probes) {
+  std::vector<uint32_t> common;
+  for (uint32_t w = w_begin; w < w_end; ++w) {
+    for (uint32_t u : g.in[w]) {
+      common.clear();
+      std::set_intersection(g.out[u].begin(), g.out[u].end(), g.in[w].begin(),
+                            g.in[w].end(), std::back_inserter(common));
+      probes += g.out[u].size();
+      for (uint32_t v : common) s.output(u, v, w);
+    }
+  }
+}
+
+void list_apm_sets(const Graph &g, uint32_t u_begin, uint32_t u_end, Sink &s,
+                   uint64_t &probes) {
+  std::vector<uint32_t> common;
+  for (uint32_t u = u_begin; u < u_end; ++u) {
+    for (uint32_t v : g.out[u]) {
+      common.clear();
+      std::set_intersection(g.out[u].begin(), g.out[u].end(), g.out[v].begin(),
+                            g.out[v].end(), std::back_inserter(common));
+      probes += g.out[v].size();
+      for (uint32_t w : common) s.output(u, v, w);
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+// Status codes: 0 ok, 1 invalid argument, 2 output buffer too small (the
+// count and hash are still complete).
+
+// Load an undirected graph from a raw edge list edges[2*m_in] of ids in
+// [0, n).  Loops are dropped and a pair listed several times, in either
+// direction, is kept once (Sec. 4.1).  The ordering starts as the identity.
+int or_graph_new(uint32_t n, const uint32_t *edges, uint64_t m_in, void **out) {
+  *out = nullptr;
+  Graph *g = new Graph;
+  g->n = n;
+  g->E.reserve(m_in);
+  for (uint64_t i = 0; i < m_in; ++i) {
+    uint32_t a = edges[2 * i], b = edges[2 * i + 1];
+    if (a >= n || b >= n) {
+      delete g;
+      return 1;
+    }
+    if (a == b) continue;
+    g->E.emplace_back(std::min(a, b), std::max(a, b));
+  }
+  std::sort(g->E.begin(), g->E.end());
+  g->E.erase(std::unique(g->E.begin(), g->E.end()), g->E.end());
+  g->rank.resize(n);
+  g->inv.resize(n);
+  for (uint32_t v = 0; v < n; ++v) g->rank[v] = g->inv[v] = v;
+  build_dag(*g);
+  *out = g;
+  return 0;
+}
+
+void or_graph_free(void *h) { delete static_cast<Graph *>(h); }
+
+uint64_t or_num_edges(const void *h) { return static_cast<const Graph *>(h)->E.size(); }
+
+// Apply ordering rank[n] (rank[v] = pi_v - 1).  Not a permutation -> 1, and
+// the previous ordering stays in force.
+int or_order_apply(void *h, const uint32_t *rank) {
+  Graph *g = static_cast<Graph *>(h);
+  std::vector<char> seen(g->n, 0);
+  for (uint32_t v = 0; v < g->n; ++v) {
+    if (rank[v] >= g->n || seen[rank[v]]) return 1;
+    seen[rank[v]] = 1;
+  }
+  for (uint32_t v = 0; v < g->n; ++v) {
+    g->rank[v] = rank[v];
+    g->inv[rank[v]] = v;
+  }
+  build_dag(*g);
+  return 0;
+}
+
+// Cost induced by the ordering (Definition of Sec. 3.1):
+//   alg 0: C++ = sum_u d+_u * d+_u      alg 1: C+- = sum_u d+_u * d-_u
+uint64_t or_cost(const void *h, int alg) {
+  const Graph *g = static_cast<const Graph *>(h);
+  uint64_t c = 0;
+  for (uint32_t x = 0; x < g->n; ++x) {
+    uint64_t dp = g->out[x].size(), dm = g->in[x].size();
+    c += (alg == 0) ? dp * dp : dp * dm;
+  }
+  return c;
+}
+
+// List triangles with Algorithm 1 (alg 0) or Algorithm 2 (alg 1), in the
+// literal boolean-array form (mode 0) or the set-intersection form (mode 1).
+// The outer loop runs over ranks [seed_begin, seed_end) (pass 0 and n for
+// the whole graph; a sub-range lists the triangles whose third vertex (A++)
+// or first vertex (A+-) lies in it).  Triples go to buf[3*cap] when buf is
+// not null.
+int or_list(const void *h, int alg, int mode, uint32_t seed_begin, uint32_t seed_end,
+            uint32_t *buf, uint64_t cap, uint64_t *count, uint64_t *hash,
+            uint64_t *probes) {
+  const Graph *g = static_cast<const Graph *>(h);
+  if (alg < 0 || alg > 1 || mode < 0 || mode > 1) return 1;
+  if (seed_end > g->n || seed_begin > seed_end) return 1;
+  Sink s;
+  s.buf = buf;
+  s.cap = cap;
+  s.g = g;
+  uint64_t p = 0;
+  if (alg == 0 && mode == 0) list_app_literal(*g, seed_begin, seed_end, s, p);
+  if (alg == 0 && mode == 1) list_app_sets(*g, seed_begin, seed_end, s, p);
+  if (alg == 1 && mode == 0) list_apm_literal(*g, seed_begin, seed_end, s, p);
+  if (alg == 1 && mode == 1) list_apm_sets(*g, seed_begin, seed_end, s, p);
+  if (count) *count = s.count;
+  if (hash) *hash = s.hash;
+  if (probes) *probes = p;
+  return (buf && s.count > cap) ? 2 : 0;
+}
+
+// Export the DAG as CSR in rank space: dir 0 = N+ (out), dir 1 = N- (in).
+// off[n+1] and adj[m] are caller-owned.
+int or_csr(const void *h, int dir, uint64_t *off, uint32_t *adj) {
+  const Graph *g = static_cast<const Graph *>(h);
+  const auto &L = (dir == 0) ? g->out : g->in;
+  uint64_t k = 0;
+  for (uint32_t x = 0; x < g->n; ++x) {
+    off[x] = k;
+    for (uint32_t y : L[x]) adj[k++] = y;
+  }
+  off[g->n] = k;
+  return 0;
+}
+
+// The set hash of caller-given triples (each must already be sorted a<b<c).
+uint64_t or_hash_triples(const uint32_t *t, uint64_t count) {
+  uint64_t hsum = 0;
+  for (uint64_t i = 0; i < count; ++i) hsum += triple_hash(t[3 * i], t[3 * i + 1], t[3 * i + 2]);
+  return hsum;
+}
+
+uint64_t or_mix64(uint64_t z) { return mix(z); }
+
+}  // extern "C"
