@@ -1,0 +1,388 @@
+#!/usr/bin/env python3
+"""Benchmark of the triangle-listing hot path on one GB300 (one JSON line).
+
+Workload: R-MAT scale 20 (1,048,576 vertices), edge factor 16, quadrant
+probabilities (0.57, 0.19, 0.19, 0.05), seed 2; symmetrised, deduplicated,
+loops removed by the library (about 15.7M undirected edges); degree
+ordering (ties by id).  One step runs the whole path once:
+graph_load (a1) -> order_apply (a2-a5: relabel, orient, CSR, cost) ->
+list_triangles A++ and list_triangles A+- (a6-a9), each listing streamed in
+1 GiB chunks to the library's device count + hash consumer.
+
+value: triangles listed per second of device time over the timed steps
+(both algorithms list the same T triangles; a step lists 2T).  e2e: the
+same step through the C ABI from pinned host buffers, host<->device copies
+included, wall clock.  roofline: the listing kernels' algorithmic bytes
+4 (C + m) + 12 T per listing over their summed CUDA-event time.
+
+--impl reference times the CPU oracle (the paper's Algorithms 1 and 2,
+single thread) on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = {"workload": "rmat20-degree", "generator": "R-MAT", "scale": 20, "edge_factor": 16,
+            "abcd": [0.57, 0.19, 0.19, 0.05], "seed": 2, "ordering": "degree (ties by id)",
+            "algorithms": ["A++", "A+-"]}
+CHUNK_BYTES = 1 << 30
+METRIC = "triangles/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def gen_inputs():
+    from paper_2203_04774_gb300 import synth
+    e = synth.rmat(WORKLOAD["scale"], WORKLOAD["edge_factor"], *WORKLOAD["abcd"][:3],
+                   WORKLOAD["seed"])
+    n = 1 << WORKLOAD["scale"]
+    deg = synth.simple_degrees(n, e)
+    rank = synth.order_degree_from_degrees(deg)
+    return n, e, rank
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def list_source_hash():
+    h = hashlib.sha256()
+    for f in ("list.cu", "list.cuh"):
+        with open(os.path.join(ROOT, "paper_2203_04774_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per listing pass from the committed ncu summary, if it was
+    taken on the current listing kernels (else None)."""
+    p = os.path.join(ROOT, "profiles", "list_rmat20_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        if d.get("list_source_sha256_16") == list_source_hash():
+            return d.get("dram_bytes_per_step")
+    except Exception:
+        pass
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_tl(args):
+    import torch
+
+    import paper_2203_04774_gb300 as tl
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    t0 = time.time()
+    n, e, rnk = gen_inputs()
+    log(f"[bench] inputs ready in {time.time() - t0:.1f}s: n={n} pairs={len(e)}")
+    stream = torch.cuda.Stream()
+    e_dev = torch.from_numpy(e).cuda()
+    r_dev = torch.from_numpy(rnk).cuda()
+    e_pin = torch.from_numpy(e).pin_memory()
+    r_pin = torch.from_numpy(rnk).pin_memory()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    ch = tl.CountHash(stream.cuda_stream)
+    ch_ptr = tl.tl_count_hash_ptr()
+
+    def step(edges, ranks):
+        g = tl.tl_graph_load(n, edges, stream.cuda_stream)
+        try:
+            tl.tl_order_apply(g, ranks)
+            m = tl.tl_graph_size(g)[1]
+            costs = [tl.tl_cost(g, a) for a in (tl.TL_APP, tl.TL_APM)]
+            out = []
+            for a in (tl.TL_APP, tl.TL_APM):
+                ch.reset()
+                nt = tl.tl_list_triangles(g, a, CHUNK_BYTES, ch_ptr, ch.user)
+                out.append((nt, int(ch.state.count), int(ch.state.hash),
+                            tl.tl_last_list_stats(g)))
+            return m, costs, out
+        finally:
+            tl.tl_graph_free(g)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step(e_dev, r_dev)
+    # timed region (device), L2 flushed before every step
+    clocks = Clocks(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    launches0 = tl.tl_kernel_launches()
+    results = []
+    barrier()
+    clocks.start()
+    for i in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        ev[i][0].record(stream)
+        results.append(step(e_dev, r_dev))
+        ev[i][1].record(stream)
+    barrier()
+    clk = clocks.stop()
+    launches = tl.tl_kernel_launches() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    m, costs, out = results[-1]
+    T = out[0][0]
+    assert all(o[0] == T and o[1] == T for r in results for o in r[2]), "triangle counts differ"
+    assert len({o[2] for r in results for o in r[2]}) == 1, "set hashes differ"
+    tri_per_step = sum(o[0] for o in out)
+    value = tri_per_step * args.steps * world / (total_ms / 1e3)
+
+    # roofline of the listing kernels (both algorithms, all launches)
+    list_ms = statistics.mean(sum(sum(o[3]["kernel_ms"]) for o in r[2]) for r in results)
+    alg_bytes = sum(4 * (c + m) + 12 * T for c in costs)
+    peak, peak_kind = read_peaks()
+    achieved = alg_bytes / (list_ms / 1e3) / 1e9
+    traffic = recorded_traffic()
+
+    # end to end through the C ABI from pinned host buffers
+    e2e_ms = []
+    for _ in range(max(2, min(args.steps, 5))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        step(e_pin, r_pin)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t1) * 1e3)
+    e2e_value = tri_per_step * len(e2e_ms) / (sum(e2e_ms) / 1e3)
+
+    per_ordering = None
+    if rank == 0 and not args.no_orderings:
+        per_ordering = ordering_sweep(tl, n, e, e_dev, stream)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(n, e, rnk)
+    ch.release()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "triangles/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic (seeded R-MAT; the paper's datasets are not available)",
+            "config": dict(WORKLOAD, n=n, m=m, triangles=T, C_pp=costs[0], C_pm=costs[1],
+                           chunk_bytes=CHUNK_BYTES, l2="256 MiB buffer written before each step",
+                           parallelism="replicas" if world > 1 else "1 GPU"),
+            "oriented_edges_per_s": m * 2 * args.steps * world / (total_ms / 1e3),
+            "e2e": {"value": e2e_value, "unit": "triangles/s",
+                    "h2d_bytes_per_step": int(e.nbytes + rnk.nbytes),
+                    "d2h_bytes_per_step": 2 * 16},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_list_small + k_list_large (A++ and A+-)",
+                         "algorithmic_bytes_per_step": alg_bytes, "kernel_ms_per_step": list_ms,
+                         "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"},
+            "kernel_ms": {a: r[3]["kernel_ms"] for a, r in zip(("A++", "A+-"), out)},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+            "per_ordering": per_ordering,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def ordering_sweep(tl, n, e, e_dev, stream):
+    """GPU listing time vs the paper's cost for several orderings (Fig. 2 analogue)."""
+    from paper_2203_04774_gb300 import synth
+    off, adj = synth.simple_csr(n, e)
+    orders = {"random": synth.order_random(n, 2), "degree": synth.order_degree(off),
+              "core": synth.order_core(off, adj), "split": synth.order_split(off),
+              "check": synth.order_check(off, adj)}
+    import torch
+    ch = tl.CountHash(stream.cuda_stream)
+    g = tl.tl_graph_load(n, e_dev, stream.cuda_stream)
+    rows = []
+    try:
+        for name, r in orders.items():
+            tl.tl_order_apply(g, torch.from_numpy(r).cuda())
+            for a, an in ((tl.TL_APP, "A++"), (tl.TL_APM, "A+-")):
+                ch.reset()
+                tl.tl_list_triangles(g, a, CHUNK_BYTES, tl.tl_count_hash_ptr(), ch.user)
+                st = tl.tl_last_list_stats(g)
+                rows.append({"ordering": name, "alg": an, "cost": tl.tl_cost(g, a),
+                             "list_kernel_ms": sum(st["kernel_ms"]), "triangles": st["triangles"]})
+    finally:
+        tl.tl_graph_free(g)
+        ch.release()
+    for an in ("A++", "A+-"):
+        xs = [r["cost"] for r in rows if r["alg"] == an]
+        ys = [r["list_kernel_ms"] for r in rows if r["alg"] == an]
+        if len(xs) > 2 and np.std(xs) > 0 and np.std(ys) > 0:
+            rows.append({"alg": an, "pearson_r_cost_vs_time": float(np.corrcoef(xs, ys)[0, 1])})
+    return rows
+
+
+def _oracle_sample_ranges(n, parts=16, frac=4):
+    """Seed-rank ranges [k n/parts, k n/parts + n/(parts*frac)): 1/frac of the
+    seed vertices, spread over the whole rank range."""
+    step = n // parts
+    width = max(1, step // frac)
+    return [(k * step, k * step + width) for k in range(parts)]
+
+
+def cpu_baseline(n, e, rnk, frac=4):
+    import oracle
+    g = oracle.Graph(n, e)
+    g.order_apply(rnk)
+    tri = 0
+    t0 = time.perf_counter()
+    for alg in (oracle.APP, oracle.APM):
+        for a, b in _oracle_sample_ranges(n, frac=frac):
+            tri += g.list(alg, oracle.LITERAL, a, b, store=False)[1]
+    dt = time.perf_counter() - t0
+    return {"value": tri / dt, "unit": "triangles/s", "cores": 1, "kind": "oracle",
+            "sample": f"Algorithms 1 and 2 (literal boolean-array form), seed ranks "
+                      f"[k n/16, k n/16 + n/{16 * frac}) for k = 0..15 (1/{frac} of the seed "
+                      f"vertices) of the same graph and degree ordering; listing only, single "
+                      f"thread; {tri} triangles in {dt:.1f} s"}
+
+
+def run_reference(args):
+    world, rank, local = dist_setup()
+    if rank != 0:
+        return
+    import oracle
+    n, e, rnk = gen_inputs()
+    g = oracle.Graph(n, e)
+    g.order_apply(rnk)
+    ranges = _oracle_sample_ranges(n, parts=16, frac=16)
+
+    def step():
+        tri = 0
+        for alg in (oracle.APP, oracle.APM):
+            for a, b in ranges:
+                tri += g.list(alg, oracle.LITERAL, a, b, store=False)[1]
+        return tri
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    tri = sum(step() for _ in range(args.steps))
+    dt = time.perf_counter() - t0
+    value = tri / dt
+    sample = ("CPU oracle (Algorithms 1 and 2, literal form, single thread) over seed ranks "
+              "[k n/16, k n/16 + n/256), k = 0..15, of R-MAT scale 20 with degree ordering; "
+              "listing only")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "triangles/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded R-MAT)",
+        "config": dict(WORKLOAD, n=n, m=g.m),
+        "cpu_baseline": {"value": value, "unit": "triangles/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "triangles/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="tl", choices=["tl", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-orderings", action="store_true", help="skip the per-ordering sweep")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_tl(args)
+
+
+if __name__ == "__main__":
+    main()

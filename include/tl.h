@@ -1,0 +1,188 @@
+/*
+ * tl.h -- triangle listing with a given vertex ordering on one GB300 GPU.
+ *
+ * C ABI of the hot path of Lecuyer, Jachiet, Magnien and Tabourier,
+ * "Tailored vertex ordering for faster triangle listing in large graphs"
+ * (arXiv:2203.04774): the "mere listing" task of Sec. 3.2 -- list every
+ * triangle of an undirected graph once, the vertex ordering being given.
+ *
+ *   tl_graph_load      load an edge list; drop loops, merge duplicate and
+ *                      reversed pairs (Sec. 4.1, dataset cleaning).
+ *   tl_order_apply     relabel the vertices by an ordering pi and orient each
+ *                      edge from lower to higher rank: the DAG G_pi of
+ *                      Sec. 1.3, stored as a rank-space CSR of sorted
+ *                      successor lists N+ and predecessor lists N-.
+ *   tl_cost            C++(pi) = sum d+_u d+_u or C+-(pi) = sum d+_u d-_u
+ *                      (Definition "Cost induced by an ordering", Sec. 3.1).
+ *   tl_list_triangles  Algorithm 1 (A++) or Algorithm 2 (A+-) of Sec. 2.1;
+ *                      each triangle is reported exactly once, in chunks of
+ *                      device memory handed to a consumer callback.
+ *
+ * Conventions common to every call
+ *   - Every call returns a tl_status; no C++ exception crosses the ABI.
+ *     On failure tl_last_error() gives a message (thread-local, valid until
+ *     the next call on the same thread).
+ *   - Vertex ids are uint32 in [0, n).  Orderings are 0-based ranks:
+ *     rank[v] = pi_v - 1, where pi is the 1-based index of Sec. 1.3.
+ *   - A graph handle owns all of its device memory.  It is not thread-safe:
+ *     use one handle per host thread.  Work is ordered on the handle's
+ *     stream (the stream given to tl_graph_load).
+ *   - "Host or device pointer" arguments say which with a flag; a device
+ *     pointer must be device memory of the current CUDA device.
+ *   - The library never falls back to the CPU: without a usable CUDA device
+ *     every call that computes returns TL_ECUDA.
+ */
+#ifndef TL_H_
+#define TL_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TL_EXPORT __attribute__((visibility("default")))
+#else
+#define TL_EXPORT
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tl_graph tl_graph; /* opaque */
+
+typedef enum {
+  TL_OK = 0,
+  TL_EINVAL = 1,     /* bad argument: NULL, id >= n, rank not a permutation */
+  TL_ENOMEM = 2,     /* device or pinned host allocation failed */
+  TL_ECUDA = 3,      /* CUDA runtime error (see tl_last_error) */
+  TL_ESTATE = 4,     /* call out of order, e.g. listing before order_apply */
+  TL_ECALLBACK = 5,  /* the consumer returned non-zero; listing stopped */
+  TL_ETIMEOUT = 6    /* a bounded device wait ran out */
+} tl_status;
+
+typedef enum {
+  TL_APP = 0, /* Algorithm 1, A++ ("L+n"): seed edge L=(u,w), scan N+_u, probe N-_w */
+  TL_APM = 1  /* Algorithm 2, A+- ("S1+n"): seed edge S1=(u,v), scan N+_v, probe N+_u */
+} tl_alg;
+
+/* Load an undirected graph.
+ *   n          number of vertices (1 <= n < 2^32 - 1).
+ *   edges      2*m_in uint32 ids, pairs (a_i, b_i) laid out a0 b0 a1 b1 ...;
+ *              host pointer if edges_on_device == 0, else device pointer.
+ *              The caller keeps ownership; the library copies what it needs.
+ *   m_in       number of pairs (may be 0).
+ *   stream     cudaStream_t (as void*) all of the handle's work is ordered
+ *              on; NULL = the legacy default stream.
+ * Loops (a == b) are dropped and a pair given several times, in either
+ * direction, is kept once (Sec. 4.1).  An id >= n -> TL_EINVAL.  The
+ * ordering starts as the identity (the "original ordering" of Sec. 2.2).
+ * On success *out owns the graph; free it with tl_graph_free. */
+TL_EXPORT tl_status tl_graph_load(tl_graph **out, uint32_t n, const uint32_t *edges,
+                        uint64_t m_in, int edges_on_device, void *stream);
+
+/* Number of vertices and of undirected edges (after cleaning). */
+TL_EXPORT tl_status tl_graph_size(const tl_graph *g, uint32_t *n, uint64_t *m);
+
+/* Apply an ordering: rank[v] = pi_v - 1 for v in [0, n), host pointer if
+ * rank_on_device == 0, else device pointer.  Builds G_pi (Sec. 1.3) as a
+ * rank-space CSR: N+_x sorted ascending (successor ranks) and N-_x sorted
+ * ascending (predecessor ranks).  Not a permutation of [0, n) ->
+ * TL_EINVAL, and the previous ordering stays in force. */
+TL_EXPORT tl_status tl_order_apply(tl_graph *g, const uint32_t *rank, int rank_on_device);
+
+/* Cost of the current ordering (Sec. 3.1): TL_APP -> C++ = sum_u d+_u^2,
+ * TL_APM -> C+- = sum_u d+_u d-_u.  Exact, uint64.  By Property 1 this is
+ * the number of neighbour tests the chosen algorithm performs. */
+TL_EXPORT tl_status tl_cost(const tl_graph *g, tl_alg alg, uint64_t *cost);
+
+/* Consumer of one chunk of triangles.  dev_triples points to n_triples
+ * records of three uint32 original vertex ids (a, b, c), a < b < c, in
+ * device memory owned by the library and valid only during the call; the
+ * consumer must have finished reading it (including device work it queued)
+ * before it returns.  chunk_index counts chunks from 0.  Chunks hold no
+ * particular order of triangles.  Return 0 to continue, non-zero to stop
+ * listing with TL_ECALLBACK. */
+typedef int (*tl_consumer)(const uint32_t *dev_triples, uint64_t n_triples,
+                           uint64_t chunk_index, void *user);
+
+/* List every triangle of the graph once (Sec. 2.1):
+ *   TL_APP: for each oriented edge (u, w), every v in N+_u that is in N-_w
+ *           gives triangle {u, v, w} (Algorithm 1);
+ *   TL_APM: for each oriented edge (u, v), every w in N+_v that is in N+_u
+ *           gives triangle {u, v, w} (Algorithm 2).
+ * Triangles are reported in original ids, sorted, in chunks of at most
+ * chunk_bytes / 12 triples (chunk_bytes >= TL_MIN_CHUNK_BYTES; two chunk
+ * buffers are allocated per call).  cb may be NULL (triangles are then only
+ * counted).  *n_triangles (may be NULL) receives the number listed.  The
+ * call returns when every chunk has been consumed. */
+#define TL_MIN_CHUNK_BYTES ((size_t)12 << 20)
+TL_EXPORT tl_status tl_list_triangles(tl_graph *g, tl_alg alg, size_t chunk_bytes,
+                            tl_consumer cb, void *user, uint64_t *n_triangles);
+
+/* Same, restricted to the seed vertices of rank [x_begin, x_end): the
+ * vertex w of Algorithm 1's outer loop (A++) or u of Algorithm 2's (A+-).
+ * Disjoint ranges list disjoint triangle sets whose union over a partition
+ * of [0, n) is the full set; this is how independent replicas split one
+ * graph.  Also returns the number of neighbour tests performed in
+ * *n_probes (may be NULL); over the full range it equals tl_cost. */
+TL_EXPORT tl_status tl_list_triangles_range(tl_graph *g, tl_alg alg, uint32_t x_begin,
+                                  uint32_t x_end, size_t chunk_bytes,
+                                  tl_consumer cb, void *user,
+                                  uint64_t *n_triangles, uint64_t *n_probes);
+
+/* A ready-made consumer: count the triples and add up their set hash
+ *   H = sum over triples of h(a,b,c)  (mod 2^64),
+ *   h(a,b,c) = mix(mix(mix(a + G) + b + G) + c + G),
+ * G = 0x9e3779b97f4a7c15, mix = the splitmix64 finaliser (Steele, Lea and
+ * Flood, OOPSLA 2014).  The sum does not depend on the order of triangles
+ * or the chunking, so it checks a large output without storing it.
+ * Pass a tl_count_hash_state* as `user`; zero it before listing.  The
+ * reduction runs on the device on `stream` and is synchronised before the
+ * consumer returns. */
+typedef struct {
+  uint64_t count;  /* out: triples seen */
+  uint64_t hash;   /* out: H */
+  void *stream;    /* in: cudaStream_t for the reduction (NULL = default) */
+  void *scratch;   /* library-owned; leave NULL, release with tl_count_hash_release */
+} tl_count_hash_state;
+TL_EXPORT int tl_count_hash(const uint32_t *dev_triples, uint64_t n_triples,
+                  uint64_t chunk_index, void *user);
+TL_EXPORT void tl_count_hash_release(tl_count_hash_state *s);
+
+/* Device copies of the DAG (rank space), for inspection and tests.
+ *   dir 0: N+ (out) lists, dir 1: N- (in) lists.
+ *   off: n+1 uint64 offsets, adj: m uint32 neighbour ranks, both host
+ *   pointers owned by the caller; rows sorted ascending. */
+TL_EXPORT tl_status tl_graph_csr(const tl_graph *g, int dir, uint64_t *off, uint32_t *adj);
+
+/* Counters of the last tl_list_triangles* call on this graph, for benches
+ * and profiling.  kernel_ms are CUDA-event durations of the listing kernels
+ * (index 0: small-vertex kernel, 1: large-vertex kernel), recorded on the
+ * handle's stream around each launch. */
+typedef struct {
+  uint64_t launches;     /* listing kernel launches */
+  uint64_t chunks;       /* chunks handed to the consumer */
+  uint64_t triangles;    /* triangles listed */
+  uint64_t probes;       /* membership tests performed */
+  uint64_t tasks[2];     /* tasks of each kernel */
+  double kernel_ms[2];   /* summed device time of each kernel */
+} tl_list_stats;
+TL_EXPORT tl_status tl_last_list_stats(const tl_graph *g, tl_list_stats *out);
+
+/* Number of CUDA kernels this library has launched since it was loaded
+ * (all threads, all graphs). */
+TL_EXPORT uint64_t tl_kernel_launches(void);
+
+/* Release the graph and all of its device memory.  NULL is a no-op. */
+TL_EXPORT void tl_graph_free(tl_graph *g);
+
+/* Message of the last failed call on this thread ("" if none). */
+TL_EXPORT const char *tl_last_error(void);
+
+/* Library version string. */
+TL_EXPORT const char *tl_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TL_H_ */

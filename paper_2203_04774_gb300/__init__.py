@@ -1,1 +1,302 @@
-"""GB300-native triangle listing with a given vertex ordering (arXiv:2203.04774)."""
+"""GB300-native triangle listing with a given vertex ordering (arXiv:2203.04774).
+
+Python binding of ``libtl.so`` (C ABI in ``include/tl.h``).  The functions
+``tl_*`` below marshal arguments and call the library; every step of the
+listing path runs in the library's CUDA kernels.  PyTorch is used only to
+hold device memory and to name streams.
+
+There is no CPU fallback: if ``libtl.so`` is missing, ``lib()`` raises.
+Build it with ``python -c "import __graft_entry__ as g; g.build()"``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtl.so")
+
+TL_OK, TL_EINVAL, TL_ENOMEM, TL_ECUDA, TL_ESTATE, TL_ECALLBACK, TL_ETIMEOUT = range(7)
+TL_APP, TL_APM = 0, 1
+TL_MIN_CHUNK_BYTES = 12 << 20
+STATUS_NAMES = {0: "TL_OK", 1: "TL_EINVAL", 2: "TL_ENOMEM", 3: "TL_ECUDA", 4: "TL_ESTATE",
+                5: "TL_ECALLBACK", 6: "TL_ETIMEOUT"}
+
+# Every symbol the header declares, with its ctypes signature.
+_P, _U32, _U64, _I, _SZ = (ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int,
+                           ctypes.c_size_t)
+CONSUMER = ctypes.CFUNCTYPE(ctypes.c_int, _P, _U64, _U64, _P)
+
+
+class CountHashState(ctypes.Structure):
+    _fields_ = [("count", _U64), ("hash", _U64), ("stream", _P), ("scratch", _P)]
+
+
+class ListStats(ctypes.Structure):
+    _fields_ = [("launches", _U64), ("chunks", _U64), ("triangles", _U64), ("probes", _U64),
+                ("tasks", _U64 * 2), ("kernel_ms", ctypes.c_double * 2)]
+
+
+SIGNATURES = {
+    "tl_graph_load": ([ctypes.POINTER(_P), _U32, _P, _U64, _I, _P], _I),
+    "tl_graph_size": ([_P, ctypes.POINTER(_U32), ctypes.POINTER(_U64)], _I),
+    "tl_order_apply": ([_P, _P, _I], _I),
+    "tl_cost": ([_P, _I, ctypes.POINTER(_U64)], _I),
+    "tl_list_triangles": ([_P, _I, _SZ, _P, _P, ctypes.POINTER(_U64)], _I),
+    "tl_list_triangles_range": ([_P, _I, _U32, _U32, _SZ, _P, _P, ctypes.POINTER(_U64),
+                                 ctypes.POINTER(_U64)], _I),
+    "tl_count_hash": ([_P, _U64, _U64, _P], _I),
+    "tl_count_hash_release": ([ctypes.POINTER(CountHashState)], None),
+    "tl_graph_csr": ([_P, _I, _P, _P], _I),
+    "tl_last_list_stats": ([_P, ctypes.POINTER(ListStats)], _I),
+    "tl_kernel_launches": ([], _U64),
+    "tl_graph_free": ([_P], None),
+    "tl_last_error": ([], ctypes.c_char_p),
+    "tl_version": ([], ctypes.c_char_p),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded CUDA library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"{LIB_PATH} is missing: the CUDA library must be built first "
+                    "(__graft_entry__.build()); there is no CPU fallback")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (args, res) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+class TLError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = lib().tl_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(status: int, where: str) -> None:
+    if status != TL_OK:
+        raise TLError(status, where)
+
+
+def _ptr_and_flag(x):
+    """(pointer, on_device, keepalive) of a numpy array or torch tensor."""
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            x = x.contiguous()
+            return x.data_ptr(), int(x.is_cuda), x
+    except ImportError:  # pragma: no cover
+        pass
+    a = np.ascontiguousarray(x, dtype=np.uint32)
+    return a.ctypes.data, 0, a
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+# ---- functions with the C names ---------------------------------------------
+
+def tl_graph_load(n: int, edges, stream=None) -> ctypes.c_void_p:
+    """Load an undirected graph from uint32 pairs [m, 2] (host numpy or device torch)."""
+    ptr, on_dev, keep = _ptr_and_flag(edges)
+    m_in = int(np.prod(keep.shape)) // 2
+    h = _P()
+    _check(lib().tl_graph_load(ctypes.byref(h), n, ptr, m_in, on_dev, _stream_handle(stream)),
+           "tl_graph_load")
+    return h
+
+
+def tl_graph_size(g) -> tuple[int, int]:
+    n, m = _U32(), _U64()
+    _check(lib().tl_graph_size(g, ctypes.byref(n), ctypes.byref(m)), "tl_graph_size")
+    return int(n.value), int(m.value)
+
+
+def tl_order_apply(g, rank) -> None:
+    ptr, on_dev, keep = _ptr_and_flag(rank)
+    _check(lib().tl_order_apply(g, ptr, on_dev), "tl_order_apply")
+
+
+def tl_cost(g, alg: int) -> int:
+    c = _U64()
+    _check(lib().tl_cost(g, alg, ctypes.byref(c)), "tl_cost")
+    return int(c.value)
+
+
+def _consumer_ptr(cb):
+    if cb is None:
+        return None, None
+    if isinstance(cb, CONSUMER):
+        return ctypes.cast(cb, _P), cb
+    if isinstance(cb, int):
+        return cb, None
+    wrapped = CONSUMER(cb)
+    return ctypes.cast(wrapped, _P), wrapped
+
+
+def tl_list_triangles(g, alg: int, chunk_bytes: int = TL_MIN_CHUNK_BYTES, cb=None,
+                      user=None) -> int:
+    cbp, keep = _consumer_ptr(cb)
+    nt = _U64()
+    _check(lib().tl_list_triangles(g, alg, chunk_bytes, cbp, user, ctypes.byref(nt)),
+           "tl_list_triangles")
+    return int(nt.value)
+
+
+def tl_list_triangles_range(g, alg: int, x_begin: int, x_end: int,
+                            chunk_bytes: int = TL_MIN_CHUNK_BYTES, cb=None,
+                            user=None) -> tuple[int, int]:
+    cbp, keep = _consumer_ptr(cb)
+    nt, npb = _U64(), _U64()
+    _check(lib().tl_list_triangles_range(g, alg, x_begin, x_end, chunk_bytes, cbp, user,
+                                         ctypes.byref(nt), ctypes.byref(npb)),
+           "tl_list_triangles_range")
+    return int(nt.value), int(npb.value)
+
+
+def tl_graph_csr(g, direction: int) -> tuple[np.ndarray, np.ndarray]:
+    n, m = tl_graph_size(g)
+    off = np.empty(n + 1, dtype=np.uint64)
+    adj = np.empty(max(m, 1), dtype=np.uint32)
+    _check(lib().tl_graph_csr(g, direction, off.ctypes.data, adj.ctypes.data), "tl_graph_csr")
+    return off, adj[:m]
+
+
+def tl_last_list_stats(g) -> dict:
+    st = ListStats()
+    _check(lib().tl_last_list_stats(g, ctypes.byref(st)), "tl_last_list_stats")
+    return {"launches": int(st.launches), "chunks": int(st.chunks),
+            "triangles": int(st.triangles), "probes": int(st.probes),
+            "tasks": [int(st.tasks[0]), int(st.tasks[1])],
+            "kernel_ms": [float(st.kernel_ms[0]), float(st.kernel_ms[1])]}
+
+
+def tl_kernel_launches() -> int:
+    return int(lib().tl_kernel_launches())
+
+
+def tl_graph_free(g) -> None:
+    if g:
+        lib().tl_graph_free(g)
+
+
+def tl_count_hash_ptr() -> int:
+    """Address of the library's count + hash consumer (pass as ``cb``)."""
+    return ctypes.cast(lib().tl_count_hash, _P).value
+
+
+# ---- conveniences -----------------------------------------------------------
+
+class _DevView:
+    """Exposes a device buffer of triples through __cuda_array_interface__."""
+
+    def __init__(self, ptr: int, n: int):
+        self.__cuda_array_interface__ = {
+            "shape": (n, 3), "typestr": "<u4", "data": (ptr, True), "version": 2}
+
+
+class Collect:
+    """Consumer that copies every chunk to host memory (tests, small graphs)."""
+
+    def __init__(self):
+        self.parts: list[np.ndarray] = []
+        self.calls = 0
+        self.fn = CONSUMER(self._on_chunk)
+
+    def _on_chunk(self, ptr, n, idx, user):
+        import torch
+        self.calls += 1
+        if n:
+            t = torch.as_tensor(_DevView(ptr, n), device="cuda")
+            self.parts.append(t.cpu().numpy().copy())
+        return 0
+
+    def triples(self) -> np.ndarray:
+        if not self.parts:
+            return np.zeros((0, 3), dtype=np.uint32)
+        return np.concatenate(self.parts).astype(np.uint32)
+
+
+class CountHash:
+    """The library's device count + hash consumer."""
+
+    def __init__(self, stream=None):
+        self.state = CountHashState(0, 0, _stream_handle(stream), None)
+
+    @property
+    def user(self):
+        return ctypes.cast(ctypes.pointer(self.state), _P)
+
+    def reset(self):
+        self.state.count = 0
+        self.state.hash = 0
+
+    def release(self):
+        lib().tl_count_hash_release(ctypes.byref(self.state))
+
+
+class Graph:
+    """A graph handle: load, order, cost, list (thin wrapper over tl_*)."""
+
+    def __init__(self, n: int, edges, stream=None):
+        self.n = n
+        self.h = tl_graph_load(n, edges, stream)
+
+    def __del__(self):
+        self.free()
+
+    def free(self):
+        h = getattr(self, "h", None)
+        if h:
+            tl_graph_free(h)
+        self.h = None
+
+    @property
+    def m(self) -> int:
+        return tl_graph_size(self.h)[1]
+
+    def order_apply(self, rank) -> None:
+        tl_order_apply(self.h, rank)
+
+    def cost(self, alg: int) -> int:
+        return tl_cost(self.h, alg)
+
+    def csr(self, direction: int):
+        return tl_graph_csr(self.h, direction)
+
+    def list_collect(self, alg: int, chunk_bytes: int = TL_MIN_CHUNK_BYTES,
+                     x_begin: int = 0, x_end: int | None = None):
+        c = Collect()
+        nt, npb = tl_list_triangles_range(self.h, alg, x_begin, self.n if x_end is None else x_end,
+                                          chunk_bytes, c.fn, None)
+        return c.triples(), nt, npb, c.calls
+
+    def list_count_hash(self, alg: int, chunk_bytes: int = TL_MIN_CHUNK_BYTES,
+                        x_begin: int = 0, x_end: int | None = None, stream=None):
+        ch = CountHash(stream)
+        try:
+            nt, npb = tl_list_triangles_range(self.h, alg, x_begin,
+                                              self.n if x_end is None else x_end, chunk_bytes,
+                                              tl_count_hash_ptr(), ch.user)
+            return nt, int(ch.state.count), int(ch.state.hash), npb
+        finally:
+            ch.release()

@@ -1,0 +1,398 @@
+// C ABI of libtl (declared in include/tl.h).
+#include <atomic>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "list.cuh"
+
+namespace tl {
+
+namespace {
+thread_local std::string g_last_error;
+std::atomic<uint64_t> g_launches{0};
+}
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+void clear_error() { g_last_error.clear(); }
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+
+// Pinned host copy of the control block (one per graph).
+struct PinnedCtl {
+  ListCtl *h = nullptr;
+  PinnedCtl() {
+    TL_CUDA(cudaMallocHost(&h, sizeof(ListCtl)));
+    std::memset(h, 0, sizeof(ListCtl));
+  }
+  ~PinnedCtl() {
+    if (h) cudaFreeHost(h);
+  }
+};
+
+}  // namespace
+}  // namespace tl
+
+struct tl_graph {
+  tl::DeviceGraph g;
+  // listing workspace
+  tl::DevBuf wseed, WP, small_w, small_prefix, pieces, piece_prefix, ctl, chunks, slabs, retry;
+  tl::PinnedCtl *pctl = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  tl_list_stats stats{};
+  int cached_alg = -1;
+  uint32_t cached_xb = 0, cached_xe = 0;
+  uint64_t n_small_tasks = 0, n_large_tasks = 0;
+  ~tl_graph() {
+    delete pctl;
+    for (auto &e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+};
+
+#define TL_API_BEGIN \
+  try {              \
+    tl::clear_error();
+#define TL_API_END                                           \
+  }                                                          \
+  catch (const tl::Error &e) {                               \
+    tl::set_error(e.msg);                                    \
+    return e.status;                                         \
+  }                                                          \
+  catch (const std::bad_alloc &) {                           \
+    tl::set_error("host allocation failed");                 \
+    return TL_ENOMEM;                                        \
+  }                                                          \
+  catch (...) {                                              \
+    tl::set_error("unexpected internal error");              \
+    return TL_ECUDA;                                         \
+  }                                                          \
+  return TL_OK;
+
+namespace {
+
+void require_device() {
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess || count == 0)
+    tl::fail(TL_ECUDA, std::string("no usable CUDA device: ") +
+                           (e != cudaSuccess ? cudaGetErrorString(e) : "device count is 0"));
+}
+
+// a6: per-seed-edge work prefix and the task counts of both kernels.
+void bucketize(tl_graph *G, int alg, uint32_t xb, uint32_t xe) {
+  if (G->cached_alg == alg && G->cached_xb == xb && G->cached_xe == xe) return;
+  tl::DeviceGraph &g = G->g;
+  cudaStream_t s = g.stream;
+  const uint64_t m = g.m;
+  const uint64_t *poff = (alg == TL_APP) ? g.in_off.as<uint64_t>() : g.out_off.as<uint64_t>();
+  const uint32_t *padj = (alg == TL_APP) ? g.in_adj.as<uint32_t>() : g.out_adj.as<uint32_t>();
+  G->wseed.reserve((m ? m : 1) * 4);
+  G->WP.reserve((m + 1) * 8);
+  if (m) tl::launch_seed_work(padj, m, g.out_off.as<uint64_t>(), G->wseed.as<uint32_t>(), s);
+  tl::exclusive_scan_u32_to_u64(G->wseed.as<uint32_t>(), G->WP.as<uint64_t>(), m, g.scan_tmp, s);
+  const uint64_t nr = xe - xb;
+  G->small_w.reserve((nr ? nr : 1) * 8);
+  G->pieces.reserve((nr ? nr : 1) * 8);
+  G->small_prefix.reserve((nr + 1) * 8);
+  G->piece_prefix.reserve((nr + 1) * 8);
+  if (nr)
+    tl::launch_classify(poff, G->WP.as<uint64_t>(), xb, xe, G->small_w.as<uint64_t>(),
+                        G->pieces.as<uint64_t>(), s);
+  tl::exclusive_scan_u64(G->small_w.as<uint64_t>(), G->small_prefix.as<uint64_t>(), nr,
+                         g.scan_tmp, s);
+  tl::exclusive_scan_u64(G->pieces.as<uint64_t>(), G->piece_prefix.as<uint64_t>(), nr,
+                         g.scan_tmp, s);
+  uint64_t tot[2];
+  TL_CUDA(cudaMemcpyAsync(&tot[0], G->small_prefix.as<uint64_t>() + nr, 8,
+                          cudaMemcpyDeviceToHost, s));
+  TL_CUDA(cudaMemcpyAsync(&tot[1], G->piece_prefix.as<uint64_t>() + nr, 8,
+                          cudaMemcpyDeviceToHost, s));
+  TL_CUDA(cudaStreamSynchronize(s));
+  G->n_small_tasks = (tot[0] + tl::kSmallWork - 1) / tl::kSmallWork;
+  G->n_large_tasks = tot[1];
+  G->cached_alg = alg;
+  G->cached_xb = xb;
+  G->cached_xe = xe;
+}
+
+struct Phase {
+  int kind;
+  uint64_t n_tasks;
+  uint64_t fresh = 0;
+  uint32_t n_retry = 0;
+};
+
+tl_status list_impl(tl_graph *G, int alg, uint32_t xb, uint32_t xe, size_t chunk_bytes,
+                    tl_consumer cb, void *user, uint64_t *n_triangles, uint64_t *n_probes) {
+  TL_API_BEGIN
+  if (!G) tl::fail(TL_EINVAL, "graph is NULL");
+  if (alg != TL_APP && alg != TL_APM) tl::fail(TL_EINVAL, "alg must be TL_APP or TL_APM");
+  tl::DeviceGraph &g = G->g;
+  if (!g.ordered) tl::fail(TL_ESTATE, "no ordering applied");
+  if (xb > xe || xe > g.n) tl::fail(TL_EINVAL, "seed range outside [0, n]");
+  if (chunk_bytes < TL_MIN_CHUNK_BYTES) tl::fail(TL_EINVAL, "chunk_bytes below TL_MIN_CHUNK_BYTES");
+  const uint64_t cap = chunk_bytes / 12;
+  if (cap < tl::kSlabCap) tl::fail(TL_EINVAL, "chunk too small for one task");
+  cudaStream_t s = g.stream;
+  bucketize(G, alg, xb, xe);
+
+  const int grid = tl::small_grid() > tl::large_grid() ? tl::small_grid() : tl::large_grid();
+  G->chunks.reserve(2 * cap * 12);
+  G->slabs.reserve((uint64_t)grid * tl::kSlabCap * 12);
+  uint64_t max_tasks = G->n_small_tasks > G->n_large_tasks ? G->n_small_tasks : G->n_large_tasks;
+  G->retry.reserve(2 * (max_tasks ? max_tasks : 1) * 4);
+  G->ctl.reserve(sizeof(tl::ListCtl));
+  if (!G->pctl) G->pctl = new tl::PinnedCtl();
+  tl::ListCtl *hc = G->pctl->h;
+  uint32_t *chunk[2] = {G->chunks.as<uint32_t>(), G->chunks.as<uint32_t>() + 3 * cap};
+  uint32_t *retry[2] = {G->retry.as<uint32_t>(),
+                        G->retry.as<uint32_t>() + (max_tasks ? max_tasks : 1)};
+
+  tl::ListArgs a{};
+  a.n = g.n;
+  a.x_begin = xb;
+  a.x_end = xe;
+  a.poff = (alg == TL_APP) ? g.in_off.as<uint64_t>() : g.out_off.as<uint64_t>();
+  a.padj = (alg == TL_APP) ? g.in_adj.as<uint32_t>() : g.out_adj.as<uint32_t>();
+  a.out_off = g.out_off.as<uint64_t>();
+  a.out_adj = g.out_adj.as<uint32_t>();
+  a.inv = g.inv.as<uint32_t>();
+  a.WP = G->WP.as<uint64_t>();
+  a.small_prefix = G->small_prefix.as<uint64_t>();
+  a.piece_prefix = G->piece_prefix.as<uint64_t>();
+  a.ctl = G->ctl.as<tl::ListCtl>();
+  a.chunk_cap = cap;
+  a.slabs = G->slabs.as<uint32_t>();
+  a.slab_cap = tl::kSlabCap;
+
+  if (!G->ev[0]) {
+    TL_CUDA(cudaEventCreate(&G->ev[0]));
+    TL_CUDA(cudaEventCreate(&G->ev[1]));
+  }
+  tl_list_stats st{};
+  st.tasks[0] = G->n_small_tasks;
+  st.tasks[1] = G->n_large_tasks;
+  G->stats = st;
+  Phase phases[2] = {{0, G->n_small_tasks}, {1, G->n_large_tasks}};
+  int cur = 0, rsel = 0;
+  uint64_t filled = 0, chunk_idx = 0, total_tri = 0, total_probes = 0;
+  int pending = -1;
+  uint64_t pending_n = 0;
+  bool stopped = false;
+  int ph = 0;
+  auto deliver = [&](int which, uint64_t cnt) {
+    if (cb && cnt > 0 && !stopped) {
+      if (cb(chunk[which], cnt, chunk_idx, user) != 0) stopped = true;
+    }
+    if (cnt > 0) ++chunk_idx;
+    st.chunks = chunk_idx;
+  };
+  for (;;) {
+    while (ph < 2 && phases[ph].fresh >= phases[ph].n_tasks && phases[ph].n_retry == 0) ++ph;
+    const bool launch = ph < 2 && !stopped;
+    Phase *P = launch ? &phases[ph] : nullptr;
+    if (launch) {
+      std::memset(hc, 0, sizeof(*hc));
+      hc->cursor = filled;
+      hc->valid_end = filled;
+      TL_CUDA(cudaMemcpyAsync(a.ctl, hc, sizeof(*hc), cudaMemcpyHostToDevice, s));
+      a.chunk = chunk[cur];
+      a.retry_in = retry[rsel];
+      a.n_retry = P->n_retry;
+      a.retry_out = retry[rsel ^ 1];
+      a.fresh_base = P->fresh;
+      a.n_tasks = P->n_tasks;
+      TL_CUDA(cudaEventRecord(G->ev[0], s));
+      tl::launch_list(P->kind, a, s);
+      TL_CUDA(cudaEventRecord(G->ev[1], s));
+      ++st.launches;
+      TL_CUDA(cudaMemcpyAsync(hc, a.ctl, sizeof(*hc), cudaMemcpyDeviceToHost, s));
+    }
+    if (pending >= 0) {  // consumer runs while the next launch is in flight
+      deliver(pending, pending_n);
+      pending = -1;
+    }
+    if (!launch) break;
+    TL_CUDA(cudaStreamSynchronize(s));
+    {
+      float ms = 0.f;
+      TL_CUDA(cudaEventElapsedTime(&ms, G->ev[0], G->ev[1]));
+      st.kernel_ms[P->kind] += ms;
+    }
+    total_tri += hc->triangles;
+    total_probes += hc->probes;
+    const uint32_t fetched = hc->fetch;
+    const uint32_t used_retry = fetched < P->n_retry ? fetched : P->n_retry;
+    uint64_t fresh_fetched = fetched > P->n_retry ? (uint64_t)(fetched - P->n_retry) : 0;
+    if (fresh_fetched > P->n_tasks - P->fresh) fresh_fetched = P->n_tasks - P->fresh;
+    uint32_t nr_out = hc->n_retry_out;
+    if (used_retry < P->n_retry) {  // retry entries nobody fetched carry over
+      TL_CUDA(cudaMemcpyAsync(retry[rsel ^ 1] + nr_out, retry[rsel] + used_retry,
+                              (size_t)(P->n_retry - used_retry) * 4, cudaMemcpyDeviceToDevice,
+                              s));
+      nr_out += P->n_retry - used_retry;
+    }
+    const bool progress = hc->valid_end > filled || fresh_fetched > 0 ||
+                          nr_out < P->n_retry + fresh_fetched || hc->triangles > 0 ||
+                          hc->probes > 0;
+    P->fresh += fresh_fetched;
+    P->n_retry = nr_out;
+    rsel ^= 1;
+    filled = hc->valid_end;
+    if (hc->overflow) {
+      if (filled == 0 && !progress) tl::fail(TL_ECUDA, "listing made no progress");
+      pending = cur;
+      pending_n = filled;
+      cur ^= 1;
+      filled = 0;
+    }
+  }
+  if (!stopped && filled > 0) deliver(cur, filled);
+  TL_CUDA(cudaStreamSynchronize(s));
+  if (n_triangles) *n_triangles = total_tri;
+  if (n_probes) *n_probes = total_probes;
+  st.triangles = total_tri;
+  st.probes = total_probes;
+  G->stats = st;
+  if (stopped) tl::fail(TL_ECALLBACK, "the consumer asked to stop");
+  TL_API_END
+}
+
+}  // namespace
+
+extern "C" {
+
+tl_status tl_graph_load(tl_graph **out, uint32_t n, const uint32_t *edges, uint64_t m_in,
+                        int edges_on_device, void *stream) {
+  TL_API_BEGIN
+  if (!out) tl::fail(TL_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n == 0 || n == 0xffffffffu) tl::fail(TL_EINVAL, "n must be in [1, 2^32 - 2]");
+  if (m_in > 0 && !edges) tl::fail(TL_EINVAL, "edges is NULL");
+  require_device();
+  tl_graph *G = new tl_graph();
+  try {
+    G->g.n = n;
+    G->g.stream = static_cast<cudaStream_t>(stream);
+    tl::build_edge_set(G->g, edges, m_in, edges_on_device != 0);
+    // identity ordering (the dataset's original ordering)
+    tl::DevBuf ident;
+    ident.reserve((uint64_t)n * 4);
+    {
+      uint32_t *h = nullptr;
+      TL_CUDA(cudaMallocHost(&h, (uint64_t)n * 4));
+      for (uint32_t v = 0; v < n; ++v) h[v] = v;
+      cudaError_t e = cudaMemcpy(ident.p, h, (uint64_t)n * 4, cudaMemcpyHostToDevice);
+      cudaFreeHost(h);
+      TL_CUDA(e);
+    }
+    tl::build_dag(G->g, ident.as<uint32_t>(), true);
+  } catch (...) {
+    delete G;
+    throw;
+  }
+  *out = G;
+  TL_API_END
+}
+
+tl_status tl_graph_size(const tl_graph *G, uint32_t *n, uint64_t *m) {
+  TL_API_BEGIN
+  if (!G) tl::fail(TL_EINVAL, "graph is NULL");
+  if (n) *n = G->g.n;
+  if (m) *m = G->g.m;
+  TL_API_END
+}
+
+tl_status tl_order_apply(tl_graph *G, const uint32_t *rank, int rank_on_device) {
+  TL_API_BEGIN
+  if (!G || !rank) tl::fail(TL_EINVAL, "graph or rank is NULL");
+  G->cached_alg = -1;
+  tl::build_dag(G->g, rank, rank_on_device != 0);
+  TL_API_END
+}
+
+tl_status tl_cost(const tl_graph *G, tl_alg alg, uint64_t *cost) {
+  TL_API_BEGIN
+  if (!G || !cost) tl::fail(TL_EINVAL, "graph or cost is NULL");
+  if (alg != TL_APP && alg != TL_APM) tl::fail(TL_EINVAL, "alg must be TL_APP or TL_APM");
+  if (!G->g.ordered) tl::fail(TL_ESTATE, "no ordering applied");
+  *cost = (alg == TL_APP) ? G->g.cost_app : G->g.cost_apm;
+  TL_API_END
+}
+
+tl_status tl_list_triangles(tl_graph *G, tl_alg alg, size_t chunk_bytes, tl_consumer cb,
+                            void *user, uint64_t *n_triangles) {
+  uint32_t n = G ? G->g.n : 0;
+  return list_impl(G, alg, 0, n, chunk_bytes, cb, user, n_triangles, nullptr);
+}
+
+tl_status tl_list_triangles_range(tl_graph *G, tl_alg alg, uint32_t x_begin, uint32_t x_end,
+                                  size_t chunk_bytes, tl_consumer cb, void *user,
+                                  uint64_t *n_triangles, uint64_t *n_probes) {
+  return list_impl(G, alg, x_begin, x_end, chunk_bytes, cb, user, n_triangles, n_probes);
+}
+
+int tl_count_hash(const uint32_t *dev_triples, uint64_t n_triples, uint64_t chunk_index,
+                  void *user) {
+  (void)chunk_index;
+  tl_count_hash_state *st = static_cast<tl_count_hash_state *>(user);
+  if (!st) return 1;
+  cudaStream_t s = static_cast<cudaStream_t>(st->stream);
+  if (!st->scratch) {
+    if (cudaMalloc(&st->scratch, 64) != cudaSuccess) return 1;
+  }
+  unsigned long long *acc = static_cast<unsigned long long *>(st->scratch);
+  unsigned long long h = 0;
+  try {
+    TL_CUDA(cudaMemsetAsync(acc, 0, 8, s));
+    tl::launch_count_hash(dev_triples, n_triples, acc, s);
+    TL_CUDA(cudaMemcpyAsync(&h, acc, 8, cudaMemcpyDeviceToHost, s));
+    TL_CUDA(cudaStreamSynchronize(s));
+  } catch (const tl::Error &e) {
+    tl::set_error(e.msg);
+    return 1;
+  }
+  st->count += n_triples;
+  st->hash += h;
+  return 0;
+}
+
+void tl_count_hash_release(tl_count_hash_state *s) {
+  if (s && s->scratch) {
+    cudaFree(s->scratch);
+    s->scratch = nullptr;
+  }
+}
+
+tl_status tl_graph_csr(const tl_graph *G, int dir, uint64_t *off, uint32_t *adj) {
+  TL_API_BEGIN
+  if (!G || !off || !adj) tl::fail(TL_EINVAL, "NULL argument");
+  if (dir != 0 && dir != 1) tl::fail(TL_EINVAL, "dir must be 0 (N+) or 1 (N-)");
+  if (!G->g.ordered) tl::fail(TL_ESTATE, "no ordering applied");
+  const tl::DeviceGraph &g = G->g;
+  const tl::DevBuf &o = dir == 0 ? g.out_off : g.in_off;
+  const tl::DevBuf &d = dir == 0 ? g.out_adj : g.in_adj;
+  TL_CUDA(cudaMemcpyAsync(off, o.p, ((uint64_t)g.n + 1) * 8, cudaMemcpyDeviceToHost, g.stream));
+  if (g.m) TL_CUDA(cudaMemcpyAsync(adj, d.p, g.m * 4, cudaMemcpyDeviceToHost, g.stream));
+  TL_CUDA(cudaStreamSynchronize(g.stream));
+  TL_API_END
+}
+
+tl_status tl_last_list_stats(const tl_graph *G, tl_list_stats *out) {
+  TL_API_BEGIN
+  if (!G || !out) tl::fail(TL_EINVAL, "NULL argument");
+  *out = G->stats;
+  TL_API_END
+}
+
+uint64_t tl_kernel_launches(void) { return tl::g_launches.load(); }
+
+void tl_graph_free(tl_graph *G) { delete G; }
+
+const char *tl_last_error(void) { return tl::g_last_error.c_str(); }
+
+const char *tl_version(void) { return "tl 0.1 (sm_103a)"; }
+
+}  // extern "C"

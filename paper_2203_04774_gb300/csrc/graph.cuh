@@ -1,0 +1,30 @@
+// The device-resident graph and the internal entry points of each step.
+#pragma once
+
+#include "common.cuh"
+
+namespace tl {
+
+// Everything a graph handle owns on the device.
+//   E        undirected simple edges, key = min_id << 32 | max_id, sorted.
+//   rank/inv current ordering: rank[v] = pi_v - 1, inv[rank[v]] = v.
+//   out_*    N+ lists (successor ranks) as CSR over ranks, rows ascending.
+//   in_*     N- lists (predecessor ranks), rows ascending.
+struct DeviceGraph {
+  uint32_t n = 0;
+  uint64_t m = 0;
+  cudaStream_t stream = nullptr;
+  bool ordered = false;
+  DevBuf E, rank, inv, out_off, out_adj, in_off, in_adj;
+  // workspaces (kept between calls so repeated calls do not reallocate)
+  DevBuf keys_a, keys_b, sort_tmp, scan_tmp, small;  // small: flags/counters
+  uint64_t cost_app = 0, cost_apm = 0;
+  uint32_t max_out_deg = 0, max_in_deg = 0;
+};
+
+// a1: copy + canonicalise + dedup (build.cu).  Throws tl::Error.
+void build_edge_set(DeviceGraph &g, const uint32_t *edges, uint64_t m_in, bool on_device);
+// a2-a5: validate the permutation, relabel, orient, CSR out/in, cost.
+void build_dag(DeviceGraph &g, const uint32_t *rank, bool on_device);
+
+}  // namespace tl

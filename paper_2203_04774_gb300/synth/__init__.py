@@ -35,11 +35,13 @@ from .orderings import (  # noqa: F401  (re-exported)
     order_check,
     order_core,
     order_degree,
+    order_degree_from_degrees,
     order_identity,
     order_neigh,
     order_random,
     order_split,
     simple_csr,
+    simple_degrees,
 )
 
 GAMMA = 0x9E3779B97F4A7C15

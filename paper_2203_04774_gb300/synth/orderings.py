@@ -74,10 +74,8 @@ def simple_csr(n: int, edges: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
     key = np.unique((lo << np.uint64(32)) | hi)
     lo = (key >> np.uint64(32)).astype(np.int64)
     hi = (key & np.uint64(0xFFFFFFFF)).astype(np.int64)
-    src = np.concatenate([lo, hi])
-    dst = np.concatenate([hi, lo])
-    order = np.lexsort((dst, src))
-    src, dst = src[order], dst[order]
+    both = np.sort(np.concatenate([lo * n + hi, hi * n + lo]))
+    src, dst = both // n, both % n
     off = np.zeros(n + 1, dtype=np.int64)
     np.cumsum(np.bincount(src, minlength=n), out=off[1:])
     return off, dst.astype(np.uint32)
@@ -85,6 +83,22 @@ def simple_csr(n: int, edges: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
 
 def degrees(off: np.ndarray) -> np.ndarray:
     return np.diff(off)
+
+
+def simple_degrees(n: int, edges: np.ndarray) -> np.ndarray:
+    """Degrees in the simple graph behind a raw edge list (no CSR built)."""
+    e = np.asarray(edges, dtype=np.uint64).reshape(-1, 2)
+    a, b = e[:, 0], e[:, 1]
+    keep = a != b
+    key = np.unique((np.minimum(a, b)[keep] << np.uint64(32)) | np.maximum(a, b)[keep])
+    lo = (key >> np.uint64(32)).astype(np.int64)
+    hi = (key & np.uint64(0xFFFFFFFF)).astype(np.int64)
+    return np.bincount(lo, minlength=n) + np.bincount(hi, minlength=n)
+
+
+def order_degree_from_degrees(deg: np.ndarray) -> np.ndarray:
+    """Non-decreasing degree, ties by increasing id."""
+    return _positions_to_rank(np.argsort(deg, kind="stable"))
 
 
 def _positions_to_rank(seq: np.ndarray) -> np.ndarray:

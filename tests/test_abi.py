@@ -1,0 +1,70 @@
+"""The C-ABI library builds, loads and exports every symbol include/tl.h declares.
+
+No compute call here: these run without a GPU.
+"""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_2203_04774_gb300 as tl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    src = open(os.path.join(ROOT, "include", "tl.h")).read()
+    return sorted(set(re.findall(r"TL_EXPORT\s+[\w\s\*]+?\b(tl_\w+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def built():
+    import __graft_entry__
+    __graft_entry__.build()
+    return tl.lib()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_symbols()
+    for must in ("tl_graph_load", "tl_order_apply", "tl_list_triangles", "tl_cost",
+                 "tl_graph_free", "tl_last_error", "tl_count_hash"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(built):
+    exported = subprocess.run(["nm", "-D", "--defined-only", tl.LIB_PATH], capture_output=True,
+                              text=True, check=True).stdout
+    syms = {line.split()[-1] for line in exported.splitlines() if " T " in line}
+    for name in _declared_symbols():
+        assert name in syms, name
+        assert hasattr(built, name)
+    # the binding wraps exactly the declared names
+    assert set(tl.SIGNATURES) == set(_declared_symbols())
+
+
+def test_version_and_error_strings_without_gpu(built):
+    assert built.tl_version().decode().startswith("tl ")
+    assert built.tl_last_error() is not None
+
+
+def test_null_arguments_rejected_without_gpu(built):
+    # argument checks come before any device work
+    assert built.tl_graph_load(None, 10, None, 0, 0, None) == tl.TL_EINVAL
+    h = ctypes.c_void_p()
+    assert built.tl_graph_load(ctypes.byref(h), 0, None, 0, 0, None) == tl.TL_EINVAL
+    assert built.tl_cost(None, 0, None) == tl.TL_EINVAL
+    assert built.tl_list_triangles(None, 0, 1 << 30, None, None, None) == tl.TL_EINVAL
+    built.tl_graph_free(None)
+
+
+def test_no_device_is_an_error_not_a_fallback(built):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import numpy as np
+    e = np.array([[0, 1], [1, 2], [0, 2]], dtype=np.uint32)
+    h = ctypes.c_void_p()
+    st = built.tl_graph_load(ctypes.byref(h), 3, e.ctypes.data, 3, 0, None)
+    assert st == tl.TL_ECUDA

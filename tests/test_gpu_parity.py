@@ -1,0 +1,259 @@
+"""CUDA path vs the CPU oracle, element by element (triangle sets are exact).
+
+Every call goes through the C ABI (libtl.so) via the thin ctypes binding.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2203_04774_gb300 as tl
+from paper_2203_04774_gb300 import synth
+from tests import _pins
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    import torch
+    torch.cuda.set_device(0)
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _orderings(n, e, which=("identity", "random", "degree", "core", "split", "check")):
+    off, adj = synth.simple_csr(n, e)
+    table = {
+        "identity": lambda: synth.order_identity(n),
+        "random": lambda: synth.order_random(n, 11),
+        "degree": lambda: synth.order_degree(off),
+        "core": lambda: synth.order_core(off, adj),
+        "split": lambda: synth.order_split(off),
+        "check": lambda: synth.order_check(off, adj),
+        "neigh": lambda: synth.order_neigh(off, adj)[0],
+    }
+    for name in which:
+        yield name, table[name]()
+
+
+def _compare(n, e, orderings, algs=(tl.TL_APP, tl.TL_APM), chunk_bytes=tl.TL_MIN_CHUNK_BYTES,
+             host_edges=False):
+    g = tl.Graph(n, e if host_edges else _dev(e))
+    ref = oracle.Graph(n, e)
+    assert g.m == ref.m
+    for name, rank in orderings:
+        g.order_apply(_dev(rank))
+        ref.order_apply(rank)
+        for d in (0, 1):
+            off_g, adj_g = g.csr(d)
+            off_r, adj_r = ref.csr(d)
+            assert np.array_equal(off_g, off_r), (name, d)
+            assert np.array_equal(adj_g, adj_r), (name, d)
+        for alg in algs:
+            assert g.cost(alg) == ref.cost(alg), (name, alg)
+            t, nt, probes, _ = g.list_collect(alg, chunk_bytes)
+            rt, rc, rh, rp = ref.list(alg)
+            assert nt == rc == len(t), (name, alg)
+            assert probes == rp == ref.cost(alg), (name, alg)  # Property 1
+            assert np.array_equal(oracle.canonical(t), oracle.canonical(rt)), (name, alg)
+            assert oracle.hash_triples(t) == rh
+    g.free()
+
+
+def test_fig3_graph_every_ordering_in_the_paper():
+    e = synth.fig3_graph()
+    seqs = ["abcdefg", "bcdeafg", "egfacdb", "ebgafdc", "egfcdab"]
+    g = tl.Graph(7, _dev(e))
+    for seq, cpm in zip(seqs, [9, 6, 3, 7, 4]):  # values printed with Fig. 3 and in Sec. 3.3.3
+        g.order_apply(_dev(synth.rank_from_sequence(seq)))
+        assert g.cost(tl.TL_APM) == cpm
+    _compare(7, e, [(s, synth.rank_from_sequence(s)) for s in seqs])
+
+
+@pytest.mark.parametrize("seed", list(range(100, 120)))
+def test_gnp_vs_oracle_and_brute_force(seed):
+    n = 50
+    e = synth.gnp(n, 0.2, seed)
+    _compare(n, e, _orderings(n, e))
+    g = tl.Graph(n, _dev(e))
+    t, nt, _, _ = g.list_collect(tl.TL_APP)
+    assert set(map(tuple, oracle.canonical(t).tolist())) == set(_pins.brute_force_triangles(n, e))
+
+
+@pytest.mark.parametrize("n", [3, 30, 100])
+def test_complete_graphs(n):
+    cpp, cpm, tri = _pins.kn_costs(n)
+    e = synth.complete(n)
+    g = tl.Graph(n, _dev(e))
+    for rank in (synth.order_identity(n), synth.order_random(n, 3)):
+        g.order_apply(_dev(rank))
+        assert (g.cost(tl.TL_APP), g.cost(tl.TL_APM)) == (cpp, cpm)
+        for alg in (tl.TL_APP, tl.TL_APM):
+            t, nt, probes, _ = g.list_collect(alg)
+            assert nt == tri and probes == (cpp if alg == tl.TL_APP else cpm)
+            assert len(set(map(tuple, t.tolist()))) == tri
+
+
+@pytest.mark.parametrize("shape", ["bipartite", "tree", "star"])
+def test_triangle_free(shape):
+    n, e = {"bipartite": (60, synth.complete_bipartite(25, 35)),
+            "tree": (5000, synth.random_tree(5000, 5)),
+            "star": (4000, synth.star(4000, 17))}[shape]
+    _compare(n, e, _orderings(n, e, ("identity", "random", "degree")))
+
+
+@pytest.mark.parametrize("d", [1, 2, 5, 12])
+def test_ld_gadget(d):
+    e, ids = synth.ld_gadget(d)
+    n = 2 * d + 2
+    seq = [ids["e"]] + ids["v"] + ids["K"][::-1]
+    rank = np.empty(n, dtype=np.uint32)
+    rank[np.array(seq)] = np.arange(n)
+    g = tl.Graph(n, _dev(e))
+    g.order_apply(_dev(rank))
+    assert g.cost(tl.TL_APP) == _pins.ld_closed_form(d)
+    assert g.list_collect(tl.TL_APP)[1] == _pins.ld_triangles(d)
+
+
+def test_config1_chung_lu_full_set():
+    """Chung-Lu n=10^4, average degree 20, exponent 2.5, seed 1, degree
+    ordering, A++ (plus A+- and other orderings): full set compare."""
+    n = 10000
+    e = synth.chung_lu(n, 20, 2.5, 1)
+    _compare(n, e, _orderings(n, e, ("degree", "core", "random", "split", "check", "neigh")))
+
+
+def test_host_edges_and_host_rank():
+    n = 3000
+    e = synth.chung_lu(n, 16, 2.2, 6)
+    g = tl.Graph(n, e)  # host pointer
+    off, _ = synth.simple_csr(n, e)
+    rank = synth.order_degree(off)
+    g.order_apply(rank)  # host pointer
+    ref = oracle.Graph(n, e)
+    ref.order_apply(rank)
+    for alg in (tl.TL_APP, tl.TL_APM):
+        t, nt, _, _ = g.list_collect(alg)
+        assert np.array_equal(oracle.canonical(t), oracle.canonical(ref.list(alg)[0]))
+
+
+def test_duplicates_loops_reversed_pairs():
+    n = 400
+    base = synth.chung_lu(n, 12, 2.4, 3)
+    noisy = np.concatenate([base, base[:, ::-1], base[: len(base) // 3],
+                            np.stack([np.arange(n), np.arange(n)], 1).astype(np.uint32)])
+    _compare(n, noisy, _orderings(n, noisy, ("degree", "random")))
+
+
+def test_edge_cases_empty_and_tiny():
+    import torch
+    for n, e in [(1, np.zeros((0, 2), np.uint32)), (5, np.zeros((0, 2), np.uint32)),
+                 (3, np.array([[1, 1], [2, 2]], np.uint32)), (2, np.array([[0, 1]], np.uint32)),
+                 (3, np.array([[0, 1], [1, 2], [2, 0]], np.uint32))]:
+        g = tl.Graph(n, e)
+        for alg in (tl.TL_APP, tl.TL_APM):
+            t, nt, probes, calls = g.list_collect(alg)
+            want = len(_pins.brute_force_triangles(n, e))
+            assert nt == want == len(t)
+        g.free()
+
+
+def test_invalid_inputs():
+    e = np.array([[0, 1], [1, 2], [0, 2]], np.uint32)
+    with pytest.raises(tl.TLError) as ei:
+        tl.Graph(3, np.array([[0, 3]], np.uint32))
+    assert ei.value.status == tl.TL_EINVAL
+    g = tl.Graph(3, _dev(e))
+    before = g.csr(0)
+    for bad in ([0, 1, 1], [0, 1, 3]):
+        with pytest.raises(tl.TLError) as ei:
+            g.order_apply(_dev(np.array(bad, np.uint32)))
+        assert ei.value.status == tl.TL_EINVAL
+    after = g.csr(0)  # previous ordering still in force
+    assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1])
+    with pytest.raises(tl.TLError) as ei:
+        tl.tl_list_triangles(g.h, tl.TL_APP, 1 << 20)
+    assert ei.value.status == tl.TL_EINVAL  # chunk below the minimum
+    with pytest.raises(tl.TLError) as ei:
+        tl.tl_list_triangles_range(g.h, tl.TL_APP, 2, 1)
+    assert ei.value.status == tl.TL_EINVAL
+
+
+def test_many_chunks_k300():
+    """4,455,100 triangles of K_300 through 12 MiB chunks (1,048,576 triples
+    each): several overflow/resume rounds, no triangle lost or repeated."""
+    n = 300
+    e = synth.complete(n)
+    g = tl.Graph(n, _dev(e))
+    g.order_apply(_dev(synth.order_random(n, 5)))
+    for alg in (tl.TL_APP, tl.TL_APM):
+        t, nt, probes, calls = g.list_collect(alg, tl.TL_MIN_CHUNK_BYTES)
+        assert nt == len(t) == 300 * 299 * 298 // 6
+        assert calls >= 5
+        assert len(np.unique(oracle.canonical(t), axis=0)) == nt
+        assert oracle.hash_triples(t) == oracle.Graph(n, e).list(alg, store=False)[2]
+
+
+def test_seed_ranges_partition():
+    n = 10000
+    e = synth.chung_lu(n, 20, 2.5, 1)
+    off, _ = synth.simple_csr(n, e)
+    rank = synth.order_degree(off)
+    g = tl.Graph(n, _dev(e))
+    g.order_apply(_dev(rank))
+    ref = oracle.Graph(n, e)
+    ref.order_apply(rank)
+    for alg in (tl.TL_APP, tl.TL_APM):
+        cuts = [0, 1, 777, 5000, 9990, n]
+        parts = []
+        for a, b in zip(cuts, cuts[1:]):
+            t, nt, probes, _ = g.list_collect(alg, x_begin=a, x_end=b)
+            rt, rc, rh, rp = ref.list(alg, seed_begin=a, seed_end=b)
+            assert nt == rc and probes == rp
+            assert np.array_equal(oracle.canonical(t), oracle.canonical(rt))
+            parts.append(t)
+        allt = np.concatenate(parts)
+        assert len(np.unique(oracle.canonical(allt), axis=0)) == len(allt)
+
+
+def test_count_hash_consumer_matches_oracle():
+    n = 10000
+    e = synth.chung_lu(n, 20, 2.5, 1)
+    off, _ = synth.simple_csr(n, e)
+    rank = synth.order_degree(off)
+    g = tl.Graph(n, _dev(e))
+    g.order_apply(_dev(rank))
+    ref = oracle.Graph(n, e)
+    ref.order_apply(rank)
+    for alg in (tl.TL_APP, tl.TL_APM):
+        nt, cnt, h, probes = g.list_count_hash(alg)
+        _, rc, rh, rp = ref.list(alg, store=False)
+        assert (nt, cnt, h, probes) == (rc, rc, rh, rp)
+
+
+def test_large_n_hash_probe_path():
+    """n above the shared-memory bitmap limit (1,572,864 ranks): the large
+    kernel probes with a shared-memory hash table, and with binary search for
+    probe sets too large for it (a star-like hub with 40,000 neighbours)."""
+    n = 2_000_000
+    e1 = synth.chung_lu(n, 4, 2.1, 12)
+    hub = np.stack([np.zeros(40000, np.uint32), np.arange(1, 40001, dtype=np.uint32)], 1)
+    ring = np.stack([np.arange(1, 40000, dtype=np.uint32), np.arange(2, 40001, dtype=np.uint32)], 1)
+    e = np.concatenate([e1, hub, ring])
+    off, _ = synth.simple_csr(n, e)
+    orders = [("degree", synth.order_degree(off)), ("identity", synth.order_identity(n)),
+              ("reverse", (n - 1 - np.arange(n)).astype(np.uint32))]
+    g = tl.Graph(n, _dev(e))
+    ref = oracle.Graph(n, e)
+    for name, rank in orders:
+        g.order_apply(_dev(rank))
+        ref.order_apply(rank)
+        for alg in (tl.TL_APP, tl.TL_APM):
+            nt, cnt, h, probes = g.list_count_hash(alg)
+            _, rc, rh, rp = ref.list(alg, store=False)
+            assert (nt, h, probes) == (rc, rh, rp), (name, alg)
