@@ -211,7 +211,7 @@ class _DevView:
 
     def __init__(self, ptr: int, n: int):
         self.__cuda_array_interface__ = {
-            "shape": (n, 3), "typestr": "<u4", "data": (ptr, True), "version": 2}
+            "shape": (n, 3), "typestr": "<u4", "data": (ptr, False), "version": 2}
 
 
 class Collect:
@@ -220,15 +220,20 @@ class Collect:
     def __init__(self):
         self.parts: list[np.ndarray] = []
         self.calls = 0
+        self.error: BaseException | None = None
         self.fn = CONSUMER(self._on_chunk)
 
     def _on_chunk(self, ptr, n, idx, user):
-        import torch
-        self.calls += 1
-        if n:
-            t = torch.as_tensor(_DevView(ptr, n), device="cuda")
-            self.parts.append(t.cpu().numpy().copy())
-        return 0
+        try:
+            import torch
+            self.calls += 1
+            if n:
+                t = torch.as_tensor(_DevView(ptr, n), device="cuda")
+                self.parts.append(t.cpu().numpy().copy())
+            return 0
+        except BaseException as e:  # surfaced by the caller after the C call returns
+            self.error = e
+            return 1
 
     def triples(self) -> np.ndarray:
         if not self.parts:
@@ -286,8 +291,14 @@ class Graph:
     def list_collect(self, alg: int, chunk_bytes: int = TL_MIN_CHUNK_BYTES,
                      x_begin: int = 0, x_end: int | None = None):
         c = Collect()
-        nt, npb = tl_list_triangles_range(self.h, alg, x_begin, self.n if x_end is None else x_end,
-                                          chunk_bytes, c.fn, None)
+        try:
+            nt, npb = tl_list_triangles_range(self.h, alg, x_begin,
+                                              self.n if x_end is None else x_end, chunk_bytes,
+                                              c.fn, None)
+        except TLError:
+            if c.error is not None:
+                raise c.error
+            raise
         return c.triples(), nt, npb, c.calls
 
     def list_count_hash(self, alg: int, chunk_bytes: int = TL_MIN_CHUNK_BYTES,

@@ -36,7 +36,9 @@ __device__ __forceinline__ void sort3(uint32_t &a, uint32_t &b, uint32_t &c) {
   if (a > b) t = a, a = b, b = t;
 }
 
-// Number of lanes j with v_j <= key, for v sorted ascending across the warp.
+// Number of lanes j with v_j <= key (0..32), for v sorted ascending across
+// the warp.  The five halving steps reach at most 31; the last lane is
+// checked on its own.
 __device__ __forceinline__ int warp_count_le(uint32_t v, uint32_t key) {
   int pos = 0;
 #pragma unroll
@@ -44,6 +46,8 @@ __device__ __forceinline__ int warp_count_le(uint32_t v, uint32_t key) {
     uint32_t e = __shfl_sync(0xffffffffu, v, pos + step - 1);
     if (e <= key) pos += step;
   }
+  const uint32_t last = __shfl_sync(0xffffffffu, v, 31);
+  if (pos == 31 && last <= key) pos = 32;
   return pos;
 }
 

@@ -85,7 +85,7 @@ def test_gnp_vs_oracle_and_brute_force(seed):
     assert set(map(tuple, oracle.canonical(t).tolist())) == set(_pins.brute_force_triangles(n, e))
 
 
-@pytest.mark.parametrize("n", [3, 30, 100])
+@pytest.mark.parametrize("n", [3, 30, 32, 33, 34, 100])
 def test_complete_graphs(n):
     cpp, cpm, tri = _pins.kn_costs(n)
     e = synth.complete(n)
