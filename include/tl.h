@@ -149,6 +149,37 @@ TL_EXPORT int tl_count_hash(const uint32_t *dev_triples, uint64_t n_triples,
                   uint64_t chunk_index, void *user);
 TL_EXPORT void tl_count_hash_release(tl_count_hash_state *s);
 
+/* The count + hash consumer again, for callers that cannot allocate device
+ * memory.  The paper has no counterpart: this is a library convenience.
+ * tl_count_hash allocates its accumulator with cudaMalloc on first use;
+ * a consumer runs while the next listing kernel is in flight, and a caller
+ * that keeps all device memory in its own pool, or must not incur the
+ * implicit device synchronisation of cudaMalloc / cudaFree at that point,
+ * cannot allocate there.  This variant calls no allocator: its scratch (one
+ * partial hash per block of 16384 triples) lives in a fixed 128 KiB
+ * file-scope device array that every GPU loading the library holds until
+ * the process exits.
+ *   - Same hash H and consumer signature as tl_count_hash.  Pass a
+ *     tl_count_hash_noalloc_state* as `user`: dev_out is caller-owned device
+ *     memory of two uint64 (count, hash); each call ADDS the chunk's count
+ *     and hash to them (zero them before listing).  The reduction runs on
+ *     `stream` and is synchronised before the call returns.
+ *   - At most TL_NOALLOC_MAX_TRIPLES triples per call; a larger n_triples is
+ *     rejected (non-zero return, message in tl_last_error) before any work.
+ *   - All calls on a device share the scratch array and leave their partials
+ *     in it; calls that overlap on the GPU race on it, so serialise them.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ * Returns 0 on success, non-zero on error. */
+#define TL_NOALLOC_MAX_TRIPLES ((uint64_t)1 << 28)
+typedef struct {
+  uint64_t *dev_out; /* in: device pointer to {count, hash}; calls add to it */
+  void *stream;      /* in: cudaStream_t for the reduction (NULL = default) */
+} tl_count_hash_noalloc_state;
+TL_EXPORT int tl_count_hash_noalloc(const uint32_t *dev_triples, uint64_t n_triples,
+                                    uint64_t chunk_index, void *user);
+
 /* Device copies of the DAG (rank space), for inspection and tests.
  *   dir 0: N+ (out) lists, dir 1: N- (in) lists.
  *   off: n+1 uint64 offsets, adj: m uint32 neighbour ranks, both host

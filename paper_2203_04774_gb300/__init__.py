@@ -35,6 +35,13 @@ class CountHashState(ctypes.Structure):
     _fields_ = [("count", _U64), ("hash", _U64), ("stream", _P), ("scratch", _P)]
 
 
+class CountHashNoallocState(ctypes.Structure):
+    _fields_ = [("dev_out", _P), ("stream", _P)]
+
+
+TL_NOALLOC_MAX_TRIPLES = 1 << 28
+
+
 class ListStats(ctypes.Structure):
     _fields_ = [("launches", _U64), ("chunks", _U64), ("triangles", _U64), ("probes", _U64),
                 ("tasks", _U64 * 2), ("kernel_ms", ctypes.c_double * 2)]
@@ -51,6 +58,7 @@ SIGNATURES = {
     "tl_count_hash": ([_P, _U64, _U64, _P], _I),
     "tl_count_hash_release": ([ctypes.POINTER(CountHashState)], None),
     "tl_graph_csr": ([_P, _I, _P, _P], _I),
+    "tl_count_hash_noalloc": ([_P, _U64, _U64, _P], _I),
     "tl_last_list_stats": ([_P, ctypes.POINTER(ListStats)], _I),
     "tl_kernel_launches": ([], _U64),
     "tl_graph_free": ([_P], None),
