@@ -38,7 +38,7 @@ import numpy as np  # noqa: E402
 WORKLOAD = {"workload": "rmat20-degree", "generator": "R-MAT", "scale": 20, "edge_factor": 16,
             "abcd": [0.57, 0.19, 0.19, 0.05], "seed": 2, "ordering": "degree (ties by id)",
             "algorithms": ["A++", "A+-"]}
-CHUNK_BYTES = 1 << 30
+DEFAULT_CHUNK_MB = 1024
 METRIC = "triangles/s"
 FALLBACK_HBM_GBS = 6800.0
 
@@ -228,14 +228,14 @@ def run_tl(args):
 
     # end to end through the C ABI from pinned host buffers
     e2e_ms = []
-    for _ in range(max(2, min(args.steps, 5))):
+    for _ in range(0 if args.no_e2e else max(2, min(args.steps, 5))):
         flush.zero_()
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         step(e_pin, r_pin)
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t1) * 1e3)
-    e2e_value = tri_per_step * len(e2e_ms) / (sum(e2e_ms) / 1e3)
+    e2e_value = tri_per_step * len(e2e_ms) / (sum(e2e_ms) / 1e3) if e2e_ms else None
 
     per_ordering = None
     if rank == 0 and not args.no_orderings:
@@ -264,7 +264,7 @@ def run_tl(args):
                          "kernel": "k_list_small + k_list_large (A++ and A+-)",
                          "algorithmic_bytes_per_step": alg_bytes, "kernel_ms_per_step": list_ms,
                          "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"},
-            "kernel_ms": {a: r[3]["kernel_ms"] for a, r in zip(("A++", "A+-"), out)},
+            "list_stats": {a: r[3] for a, r in zip(("A++", "A+-"), out)},
             "gpu_launches": launches,
             "clocks": clk,
             "cpu_baseline": cpu,
@@ -377,7 +377,17 @@ def main():
     ap.add_argument("--impl", default="tl", choices=["tl", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-orderings", action="store_true", help="skip the per-ordering sweep")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--scale", type=int, default=20,
+                    help="R-MAT scale (20 is the measured workload; smaller for profiling)")
+    ap.add_argument("--chunk-mb", type=int, default=DEFAULT_CHUNK_MB,
+                    help="output chunk size in MiB")
     args = ap.parse_args()
+    global CHUNK_BYTES
+    CHUNK_BYTES = args.chunk_mb << 20
+    if args.scale != 20:
+        WORKLOAD["scale"] = args.scale
+        WORKLOAD["workload"] = f"rmat{args.scale}-degree"
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -188,15 +188,17 @@ TL_EXPORT tl_status tl_graph_csr(const tl_graph *g, int dir, uint64_t *off, uint
 
 /* Counters of the last tl_list_triangles* call on this graph, for benches
  * and profiling.  kernel_ms are CUDA-event durations of the listing kernels
- * (index 0: small-vertex kernel, 1: large-vertex kernel), recorded on the
+ * (index 0: small-, 1: medium-, 2: mid-, 3: large-vertex kernel), recorded on the
  * handle's stream around each launch. */
 typedef struct {
   uint64_t launches;     /* listing kernel launches */
   uint64_t chunks;       /* chunks handed to the consumer */
   uint64_t triangles;    /* triangles listed */
   uint64_t probes;       /* membership tests performed */
-  uint64_t tasks[2];     /* tasks of each kernel */
-  double kernel_ms[2];   /* summed device time of each kernel */
+  uint64_t tasks[4];     /* tasks of each kernel: 0 small, 1 medium, 2 mid, 3 large */
+  double kernel_ms[4];   /* summed device time of each kernel */
+  uint64_t kernel_probes[4];     /* membership tests done by each kernel */
+  uint64_t kernel_triangles[4];  /* triangles found by each kernel */
 } tl_list_stats;
 TL_EXPORT tl_status tl_last_list_stats(const tl_graph *g, tl_list_stats *out);
 

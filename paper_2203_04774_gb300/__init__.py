@@ -44,7 +44,8 @@ TL_NOALLOC_MAX_TRIPLES = 1 << 28
 
 class ListStats(ctypes.Structure):
     _fields_ = [("launches", _U64), ("chunks", _U64), ("triangles", _U64), ("probes", _U64),
-                ("tasks", _U64 * 2), ("kernel_ms", ctypes.c_double * 2)]
+                ("tasks", _U64 * 4), ("kernel_ms", ctypes.c_double * 4),
+                ("kernel_probes", _U64 * 4), ("kernel_triangles", _U64 * 4)]
 
 
 SIGNATURES = {
@@ -194,8 +195,10 @@ def tl_last_list_stats(g) -> dict:
     _check(lib().tl_last_list_stats(g, ctypes.byref(st)), "tl_last_list_stats")
     return {"launches": int(st.launches), "chunks": int(st.chunks),
             "triangles": int(st.triangles), "probes": int(st.probes),
-            "tasks": [int(st.tasks[0]), int(st.tasks[1])],
-            "kernel_ms": [float(st.kernel_ms[0]), float(st.kernel_ms[1])]}
+            "tasks": [int(v) for v in st.tasks],
+            "kernel_ms": [float(v) for v in st.kernel_ms],
+            "kernel_probes": [int(v) for v in st.kernel_probes],
+            "kernel_triangles": [int(v) for v in st.kernel_triangles]}
 
 
 def tl_kernel_launches() -> int:

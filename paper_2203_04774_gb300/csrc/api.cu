@@ -37,13 +37,18 @@ struct PinnedCtl {
 struct tl_graph {
   tl::DeviceGraph g;
   // listing workspace
-  tl::DevBuf wseed, WP, small_w, small_prefix, pieces, piece_prefix, ctl, chunks, slabs, retry;
+  tl::DevBuf wseed, WP, ctl, chunks, slabs, retry;
+  // per-vertex classification (tiers 0, 1: weights and flags; tiers 2, 3: pieces),
+  // their prefixes, and the compacted vertex lists of tiers 0 and 1
+  tl::DevBuf tw[2], tf[2], tpref[2], tpos[2], tx[2], twp[2], tstart[2], pieces[2],
+      piece_prefix[2];
   tl::PinnedCtl *pctl = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr};
   tl_list_stats stats{};
   int cached_alg = -1;
   uint32_t cached_xb = 0, cached_xe = 0;
-  uint64_t n_small_tasks = 0, n_large_tasks = 0;
+  uint64_t n_tasks[tl::kTiers] = {0, 0, 0, 0};
+  uint64_t tier_count[2] = {0, 0};
   ~tl_graph() {
     delete pctl;
     for (auto &e : ev)
@@ -93,25 +98,56 @@ void bucketize(tl_graph *G, int alg, uint32_t xb, uint32_t xe) {
   if (m) tl::launch_seed_work(padj, m, g.out_off.as<uint64_t>(), G->wseed.as<uint32_t>(), s);
   tl::exclusive_scan_u32_to_u64(G->wseed.as<uint32_t>(), G->WP.as<uint64_t>(), m, g.scan_tmp, s);
   const uint64_t nr = xe - xb;
-  G->small_w.reserve((nr ? nr : 1) * 8);
-  G->pieces.reserve((nr ? nr : 1) * 8);
-  G->small_prefix.reserve((nr + 1) * 8);
-  G->piece_prefix.reserve((nr + 1) * 8);
+  const uint64_t nr1 = nr ? nr : 1;
+  for (int t = 0; t < 2; ++t) {
+    G->tw[t].reserve(nr1 * 8);
+    G->tf[t].reserve(nr1 * 4);
+    G->tpref[t].reserve((nr + 1) * 8);
+    G->tpos[t].reserve((nr + 1) * 8);
+    G->tx[t].reserve(nr1 * 4);
+    G->twp[t].reserve((nr + 1) * 8);
+  }
+  for (int t = 0; t < 2; ++t) {
+    G->pieces[t].reserve(nr1 * 8);
+    G->piece_prefix[t].reserve((nr + 1) * 8);
+  }
   if (nr)
-    tl::launch_classify(poff, G->WP.as<uint64_t>(), xb, xe, G->small_w.as<uint64_t>(),
-                        G->pieces.as<uint64_t>(), s);
-  tl::exclusive_scan_u64(G->small_w.as<uint64_t>(), G->small_prefix.as<uint64_t>(), nr,
-                         g.scan_tmp, s);
-  tl::exclusive_scan_u64(G->pieces.as<uint64_t>(), G->piece_prefix.as<uint64_t>(), nr,
-                         g.scan_tmp, s);
-  uint64_t tot[2];
-  TL_CUDA(cudaMemcpyAsync(&tot[0], G->small_prefix.as<uint64_t>() + nr, 8,
+    tl::launch_classify(poff, G->WP.as<uint64_t>(), xb, xe, G->tw[0].as<uint64_t>(),
+                        G->tw[1].as<uint64_t>(), G->tf[0].as<uint32_t>(), G->tf[1].as<uint32_t>(),
+                        G->pieces[0].as<uint64_t>(), G->pieces[1].as<uint64_t>(), s);
+  for (int t = 0; t < 2; ++t) {
+    tl::exclusive_scan_u64(G->tw[t].as<uint64_t>(), G->tpref[t].as<uint64_t>(), nr, g.scan_tmp, s);
+    tl::exclusive_scan_u32_to_u64(G->tf[t].as<uint32_t>(), G->tpos[t].as<uint64_t>(), nr,
+                                  g.scan_tmp, s);
+    tl::launch_compact_tier(G->tf[t].as<uint32_t>(), G->tpos[t].as<uint64_t>(),
+                            G->tpref[t].as<uint64_t>(), xb, nr, G->tx[t].as<uint32_t>(),
+                            G->twp[t].as<uint64_t>(), s);
+  }
+  for (int t = 0; t < 2; ++t)
+    tl::exclusive_scan_u64(G->pieces[t].as<uint64_t>(), G->piece_prefix[t].as<uint64_t>(), nr,
+                           g.scan_tmp, s);
+  // totals: weights of tiers 0 and 1, their vertex counts, pieces of tiers 2 and 3
+  uint64_t tot[6];
+  TL_CUDA(cudaMemcpyAsync(&tot[0], G->tpref[0].as<uint64_t>() + nr, 8, cudaMemcpyDeviceToHost, s));
+  TL_CUDA(cudaMemcpyAsync(&tot[1], G->tpref[1].as<uint64_t>() + nr, 8, cudaMemcpyDeviceToHost, s));
+  TL_CUDA(cudaMemcpyAsync(&tot[2], G->tpos[0].as<uint64_t>() + nr, 8, cudaMemcpyDeviceToHost, s));
+  TL_CUDA(cudaMemcpyAsync(&tot[3], G->tpos[1].as<uint64_t>() + nr, 8, cudaMemcpyDeviceToHost, s));
+  TL_CUDA(cudaMemcpyAsync(&tot[4], G->piece_prefix[0].as<uint64_t>() + nr, 8,
                           cudaMemcpyDeviceToHost, s));
-  TL_CUDA(cudaMemcpyAsync(&tot[1], G->piece_prefix.as<uint64_t>() + nr, 8,
+  TL_CUDA(cudaMemcpyAsync(&tot[5], G->piece_prefix[1].as<uint64_t>() + nr, 8,
                           cudaMemcpyDeviceToHost, s));
   TL_CUDA(cudaStreamSynchronize(s));
-  G->n_small_tasks = (tot[0] + tl::kSmallWork - 1) / tl::kSmallWork;
-  G->n_large_tasks = tot[1];
+  G->n_tasks[0] = (tot[0] + tl::kWarpWork - 1) / tl::kWarpWork;
+  G->n_tasks[1] = (tot[1] + tl::kWarpWork - 1) / tl::kWarpWork;
+  G->n_tasks[2] = tot[4];
+  G->n_tasks[3] = tot[5];
+  G->tier_count[0] = tot[2];
+  G->tier_count[1] = tot[3];
+  for (int t = 0; t < 2; ++t) {
+    G->tstart[t].reserve((G->n_tasks[t] + 1) * 4);
+    tl::launch_task_bounds(G->twp[t].as<uint64_t>(), G->tier_count[t], G->n_tasks[t],
+                           G->tstart[t].as<uint32_t>(), s);
+  }
   G->cached_alg = alg;
   G->cached_xb = xb;
   G->cached_xe = xe;
@@ -138,17 +174,22 @@ tl_status list_impl(tl_graph *G, int alg, uint32_t xb, uint32_t xe, size_t chunk
   cudaStream_t s = g.stream;
   bucketize(G, alg, xb, xe);
 
-  const int grid = tl::small_grid() > tl::large_grid() ? tl::small_grid() : tl::large_grid();
+  uint64_t slab_words = 0, max_tasks = 1;
+  for (int t = 0; t < tl::kTiers; ++t) {
+    // warp tiers: one slab per warp; mid and large tiers: one per CTA
+    const uint64_t w =
+        (uint64_t)tl::tier_grid(t) * (t < 2 ? (tl::kWarpThreads / 32) : 1) * tl::slab_cap(t);
+    slab_words = w > slab_words ? w : slab_words;
+    max_tasks = G->n_tasks[t] > max_tasks ? G->n_tasks[t] : max_tasks;
+  }
   G->chunks.reserve(2 * cap * 12);
-  G->slabs.reserve((uint64_t)grid * tl::kSlabCap * 12);
-  uint64_t max_tasks = G->n_small_tasks > G->n_large_tasks ? G->n_small_tasks : G->n_large_tasks;
-  G->retry.reserve(2 * (max_tasks ? max_tasks : 1) * 4);
+  G->slabs.reserve(slab_words * 12);
+  G->retry.reserve(2 * max_tasks * 4);
   G->ctl.reserve(sizeof(tl::ListCtl));
   if (!G->pctl) G->pctl = new tl::PinnedCtl();
   tl::ListCtl *hc = G->pctl->h;
   uint32_t *chunk[2] = {G->chunks.as<uint32_t>(), G->chunks.as<uint32_t>() + 3 * cap};
-  uint32_t *retry[2] = {G->retry.as<uint32_t>(),
-                        G->retry.as<uint32_t>() + (max_tasks ? max_tasks : 1)};
+  uint32_t *retry[2] = {G->retry.as<uint32_t>(), G->retry.as<uint32_t>() + max_tasks};
 
   tl::ListArgs a{};
   a.n = g.n;
@@ -160,22 +201,20 @@ tl_status list_impl(tl_graph *G, int alg, uint32_t xb, uint32_t xe, size_t chunk
   a.out_adj = g.out_adj.as<uint32_t>();
   a.inv = g.inv.as<uint32_t>();
   a.WP = G->WP.as<uint64_t>();
-  a.small_prefix = G->small_prefix.as<uint64_t>();
-  a.piece_prefix = G->piece_prefix.as<uint64_t>();
   a.ctl = G->ctl.as<tl::ListCtl>();
   a.chunk_cap = cap;
   a.slabs = G->slabs.as<uint32_t>();
-  a.slab_cap = tl::kSlabCap;
 
   if (!G->ev[0]) {
     TL_CUDA(cudaEventCreate(&G->ev[0]));
     TL_CUDA(cudaEventCreate(&G->ev[1]));
   }
   tl_list_stats st{};
-  st.tasks[0] = G->n_small_tasks;
-  st.tasks[1] = G->n_large_tasks;
+  for (int t = 0; t < tl::kTiers; ++t) st.tasks[t] = G->n_tasks[t];
   G->stats = st;
-  Phase phases[2] = {{0, G->n_small_tasks}, {1, G->n_large_tasks}};
+  constexpr int kPhases = tl::kTiers;
+  Phase phases[kPhases] = {
+      {0, G->n_tasks[0]}, {1, G->n_tasks[1]}, {2, G->n_tasks[2]}, {3, G->n_tasks[3]}};
   int cur = 0, rsel = 0;
   uint64_t filled = 0, chunk_idx = 0, total_tri = 0, total_probes = 0;
   int pending = -1;
@@ -190,8 +229,8 @@ tl_status list_impl(tl_graph *G, int alg, uint32_t xb, uint32_t xe, size_t chunk
     st.chunks = chunk_idx;
   };
   for (;;) {
-    while (ph < 2 && phases[ph].fresh >= phases[ph].n_tasks && phases[ph].n_retry == 0) ++ph;
-    const bool launch = ph < 2 && !stopped;
+    while (ph < kPhases && phases[ph].fresh >= phases[ph].n_tasks && phases[ph].n_retry == 0) ++ph;
+    const bool launch = ph < kPhases && !stopped;
     Phase *P = launch ? &phases[ph] : nullptr;
     if (launch) {
       std::memset(hc, 0, sizeof(*hc));
@@ -204,6 +243,15 @@ tl_status list_impl(tl_graph *G, int alg, uint32_t xb, uint32_t xe, size_t chunk
       a.retry_out = retry[rsel ^ 1];
       a.fresh_base = P->fresh;
       a.n_tasks = P->n_tasks;
+      a.slab_cap = tl::slab_cap(P->kind);
+      a.tier = P->kind;
+      if (P->kind >= 2) a.piece_prefix = G->piece_prefix[P->kind - 2].as<uint64_t>();
+      if (P->kind < 2) {
+        a.tier_x = G->tx[P->kind].as<uint32_t>();
+        a.tier_wp = G->twp[P->kind].as<uint64_t>();
+        a.task_start = G->tstart[P->kind].as<uint32_t>();
+        a.tier_count = G->tier_count[P->kind];
+      }
       TL_CUDA(cudaEventRecord(G->ev[0], s));
       tl::launch_list(P->kind, a, s);
       TL_CUDA(cudaEventRecord(G->ev[1], s));
@@ -223,6 +271,8 @@ tl_status list_impl(tl_graph *G, int alg, uint32_t xb, uint32_t xe, size_t chunk
     }
     total_tri += hc->triangles;
     total_probes += hc->probes;
+    st.kernel_triangles[P->kind] += hc->triangles;
+    st.kernel_probes[P->kind] += hc->probes;
     const uint32_t fetched = hc->fetch;
     const uint32_t used_retry = fetched < P->n_retry ? fetched : P->n_retry;
     uint64_t fresh_fetched = fetched > P->n_retry ? (uint64_t)(fetched - P->n_retry) : 0;

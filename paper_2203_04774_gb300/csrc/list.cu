@@ -7,27 +7,33 @@
 // (A++: u=y, v=z, w=x; A+-: u=x, v=y, w=z).  The number of membership tests
 // is sum_{y in P_x} d+_y per x; summed over x it is C++ resp. C+- (Property 1).
 //
-// Work decomposition (a6).  Seed edge k = (x, y_k) is the k-th entry of the
-// probe-side CSR; it owns the d+(y_k) work items [WP[k], WP[k+1]) of a global
-// exclusive prefix WP.  Vertices with |P_x| <= 32 and little work are "small":
-// a warp holds P_x in registers (one element per lane) and probes by binary
-// search over the lanes.  The others are "large": a CTA holds P_x in shared
-// memory (a bitmap over all ranks when n is small enough -- literally the
-// boolean array B of Algorithms 1 and 2 -- else an open-addressing hash) and
-// its work range is cut into pieces of at most kPieceWork items.
+// Work space (a6).  Seed edge k = (x, y_k) is the k-th entry of the
+// probe-side CSR; it owns the d+(y_k) tests [WP[k], WP[k+1]) of a global
+// exclusive prefix WP.  Every kernel walks the tests of a range with the same
+// warp-level mapping (scan_items): a window of 32 consecutive seed edges is
+// held one per lane, each 32-test step finds every lane's seed edge by a
+// shuffle binary search over the window, so all lanes work whatever the list
+// lengths are.
 //
-// Output (a9).  A CTA appends its triangles, as sorted original ids, to a
-// private slab; at the end of a task it reserves room in the current output
-// chunk with one atomic and copies the slab there.  If the chunk is full the
-// task is queued for the next launch (after the consumer has drained the
-// chunk) and nothing of it is written, so every chunk holds whole tasks and
-// the listing resumes exactly where it stopped.
+// B (the boolean array of Algorithms 1 and 2) per tier:
+//   small/medium x: a per-warp open-addressing hash table in shared memory
+//   (load <= 1/2), one warp per x, vertices grouped into tasks of ~2^14 tests;
+//   large x: one table per CTA -- a bitmap over all ranks when n is small
+//   enough (literally B, bit-packed), else a hash table, else binary search
+//   in the sorted row -- and the work cut into pieces shared by the CTA's warps.
+//
+// Output (a9).  Hits are compacted per warp (ballot) into the CTA's private
+// slab as sorted original-id triples.  At the end of a task one atomic
+// reserves room in the current output chunk and the CTA copies the slab.
+// If the chunk is full the task is queued for the next launch (after the
+// consumer has drained the chunk) and nothing of it is written, so every
+// chunk holds whole tasks and the listing resumes exactly where it stopped.
 #include "list.cuh"
 
 namespace tl {
 namespace {
 
-constexpr uint32_t kNone = 0xffffffffu;
+constexpr uint32_t kEmpty = 0xffffffffu;
 
 __device__ __forceinline__ void sort3(uint32_t &a, uint32_t &b, uint32_t &c) {
   uint32_t t;
@@ -36,9 +42,9 @@ __device__ __forceinline__ void sort3(uint32_t &a, uint32_t &b, uint32_t &c) {
   if (a > b) t = a, a = b, b = t;
 }
 
-// Number of lanes j with v_j <= key (0..32), for v sorted ascending across
-// the warp.  The five halving steps reach at most 31; the last lane is
-// checked on its own.
+// Number of lanes j with v_j <= key (0..32), for v ascending across the
+// warp.  The five halving steps reach at most 31; the last lane is checked
+// on its own.
 __device__ __forceinline__ int warp_count_le(uint32_t v, uint32_t key) {
   int pos = 0;
 #pragma unroll
@@ -51,7 +57,53 @@ __device__ __forceinline__ int warp_count_le(uint32_t v, uint32_t key) {
   return pos;
 }
 
-// Task fetch shared by both kernels: returns the task id or -1.  Thread 0
+__device__ __forceinline__ uint64_t shfl_u64(uint64_t v, int src) {
+  uint32_t lo = __shfl_sync(0xffffffffu, (uint32_t)v, src);
+  uint32_t hi = __shfl_sync(0xffffffffu, (uint32_t)(v >> 32), src);
+  return ((uint64_t)hi << 32) | lo;
+}
+
+__device__ __forceinline__ uint64_t upper_bound_u64(const uint64_t *v, uint64_t n, uint64_t key) {
+  uint64_t lo = 0, hi = n;
+  while (lo < hi) {
+    uint64_t mid = (lo + hi) >> 1;
+    if (v[mid] <= key) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ uint64_t lower_bound_u64(const uint64_t *v, uint64_t n, uint64_t key) {
+  uint64_t lo = 0, hi = n;
+  while (lo < hi) {
+    uint64_t mid = (lo + hi) >> 1;
+    if (v[mid] < key) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// Multiplicative hash into a table of 2^lg slots.
+__device__ __forceinline__ uint32_t hslot(uint32_t r, int lg) {
+  return (r * 0x9E3779B1u) >> (32 - lg);
+}
+
+__device__ __forceinline__ void hash_insert(uint32_t *H, int lg, uint32_t r) {
+  const uint32_t mask = (1u << lg) - 1u;
+  uint32_t h = hslot(r, lg);
+  while (atomicCAS(&H[h], kEmpty, r) != kEmpty) h = (h + 1) & mask;
+}
+
+__device__ __forceinline__ bool hash_find(const uint32_t *H, int lg, uint32_t z) {
+  const uint32_t mask = (1u << lg) - 1u;
+  uint32_t h = hslot(z, lg);
+  for (;;) {
+    uint32_t v = H[h];
+    if (v == z) return true;
+    if (v == kEmpty) return false;
+    h = (h + 1) & mask;
+  }
+}
+
+// Task fetch shared by all kernels: returns the task id or -1.  Thread 0
 // only; the caller broadcasts.
 __device__ __forceinline__ int64_t fetch_task(ListCtl *ctl, const ListArgs &a) {
   if (*(volatile uint32_t *)&ctl->overflow) return -1;
@@ -59,6 +111,20 @@ __device__ __forceinline__ int64_t fetch_task(ListCtl *ctl, const ListArgs &a) {
   if (idx < a.n_retry) return a.retry_in[idx];
   uint64_t t = a.fresh_base + (idx - a.n_retry);
   return (t < a.n_tasks) ? (int64_t)t : -1;
+}
+
+// Copy a task's slab to the chunk: each slab entry is (original id of x,
+// original id of y, rank of z); z is translated and the triple sorted here,
+// where all gathers of the task are independent.
+__device__ __forceinline__ void copy_out(const ListArgs &a, const uint32_t *slab, uint32_t cnt,
+                                         uint32_t *dst, uint32_t tid, uint32_t nthreads) {
+  for (uint32_t i = tid; i < cnt; i += nthreads) {
+    uint32_t t0 = slab[3 * i], t1 = slab[3 * i + 1], t2 = a.inv[slab[3 * i + 2]];
+    sort3(t0, t1, t2);
+    dst[3 * i] = t0;
+    dst[3 * i + 1] = t1;
+    dst[3 * i + 2] = t2;
+  }
 }
 
 // End of a task: reserve chunk room for the slab, copy it, or queue the task.
@@ -89,185 +155,243 @@ __device__ void commit_task(ListCtl *ctl, const ListArgs &a, int64_t t, const ui
   }
   __syncthreads();
   if (*s_ok && cnt > 0) {
-    uint32_t *dst = a.chunk + 3ull * (*s_pos);
-    const uint32_t words = 3u * cnt;
-    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) dst[i] = slab[i];
+    copy_out(a, slab, cnt, a.chunk + 3ull * (*s_pos), threadIdx.x, blockDim.x);
   }
   __syncthreads();
 }
 
-// ---- small vertices: one warp per x, P_x in registers ------------------------
-
-__device__ __forceinline__ void list_small_x(const ListArgs &a, uint32_t x, uint32_t *slab,
-                                             uint32_t *s_cnt, unsigned long long &probes) {
+// Warp-level end of a warp-tier task: reserve chunk room for the warp's slab
+// and copy it, or queue the task.
+__device__ void commit_warp(ListCtl *ctl, const ListArgs &a, int64_t t, const uint32_t *slab,
+                            uint32_t cnt, unsigned long long probes) {
   const int lane = threadIdx.x & 31;
-  const uint64_t pb = a.poff[x];
-  const int p = (int)(a.poff[x + 1] - pb);
-  const uint32_t P = (lane < p) ? a.padj[pb + lane] : kNone;  // ascending, padded
-  uint32_t len = 0, invP = 0;
-  uint64_t st = 0;
-  if (lane < p) {
-    st = a.out_off[P];
-    len = (uint32_t)(a.out_off[P + 1] - st);
-    invP = a.inv[P];
+  uint32_t ok = 1;
+  unsigned long long pos = 0;
+  if (lane == 0) {
+    if (cnt > 0) {
+      pos = atomicAdd(&ctl->cursor, (unsigned long long)cnt);
+      if (pos + cnt > a.chunk_cap) ok = 0;
+    }
+    if (ok) {
+      if (cnt > 0) {
+        atomicMax(&ctl->valid_end, pos + cnt);
+        atomicAdd(&ctl->triangles, (unsigned long long)cnt);
+      }
+      atomicAdd(&ctl->probes, probes);
+    } else {
+      atomicExch(&ctl->overflow, 1u);
+      const uint32_t r = atomicAdd(&ctl->n_retry_out, 1u);
+      a.retry_out[r] = (uint32_t)t;
+    }
   }
-  uint32_t end = len;  // inclusive scan of the scanned-list lengths
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    uint32_t o = __shfl_up_sync(0xffffffffu, end, d);
-    if (lane >= d) end += o;
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  pos = (unsigned long long)__shfl_sync(0xffffffffu, (long long)pos, 0);
+  if (ok && cnt > 0) {
+    copy_out(a, slab, cnt, a.chunk + 3ull * pos, lane, 32);
   }
-  const uint32_t beg = end - len;
-  const uint32_t W = __shfl_sync(0xffffffffu, end, 31);
-  const uint32_t inv_x = a.inv[x];
+  __syncwarp();
+}
+
+// Warp-level walk of the tests [i0, i1) of B vertex x, whose probe-side row
+// is [pb, pe); k0 is the seed edge holding test i0 (found by binary search
+// when ~0).  For each test: z = the scanned element, member(z) = B[z]; hits
+// are appended as sorted original ids to the slab, at positions reserved from
+// the warp's own count (kWarpSlab) or from the CTA's shared count *s_cnt.
+template <bool kWarpSlab, class Member>
+__device__ __forceinline__ void scan_items(const ListArgs &a, uint64_t pb, uint64_t pe, uint64_t k0,
+                                           uint64_t i0, uint64_t i1, uint32_t inv_x,
+                                           Member member, uint32_t *slab, uint32_t *s_cnt,
+                                           uint32_t &wcnt, unsigned long long &probes) {
+  if (i0 >= i1) return;
+  const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
-  for (uint32_t base = 0; base < W; base += 32) {
-    const uint32_t i = base + lane;
-    const bool act = i < W;
-    int seg = warp_count_le(end, i);  // first segment whose end > i
-    seg = seg > 31 ? 31 : seg;
-    const uint32_t sb = __shfl_sync(0xffffffffu, beg, seg);
-    const uint64_t ss = __shfl_sync(0xffffffffu, st, seg);
-    const uint32_t iy = __shfl_sync(0xffffffffu, invP, seg);
-    uint32_t z = act ? a.out_adj[ss + (i - sb)] : 0u;
-    const int q = warp_count_le(P, z);
-    const uint32_t pz = __shfl_sync(0xffffffffu, P, q > 0 ? q - 1 : 0);
-    const bool hit = act && q > 0 && pz == z;
-    probes += act ? 1 : 0;
+  // seed edge holding test i0
+  uint64_t k = (k0 != ~0ull) ? k0 : pb + upper_bound_u64(a.WP + pb, pe - pb, i0) - 1;
+  uint64_t E = 0, A = 0, Elast = 0;
+  uint32_t iy = 0;
+  auto load_window = [&](uint64_t kw) {
+    const uint64_t kk = kw + lane;
+    const bool valid = kk < pe;
+    uint64_t B = ~0ull;
+    E = ~0ull;
+    A = 0;
+    iy = 0;
+    if (valid) {
+      B = a.WP[kk];
+      E = a.WP[kk + 1];
+      const uint32_t y = a.padj[kk];
+      A = a.out_off[y] - B;  // scanned element of test i is out_adj[A + i]
+      iy = a.inv[y];
+    }
+    Elast = shfl_u64(E, 31);
+  };
+  load_window(k);
+  // append the warp's hits of one step to the slab
+  auto emit = [&](bool hit, uint32_t iyj, uint32_t z) {
     const unsigned hm = __ballot_sync(0xffffffffu, hit);
-    if (hm) {
-      uint32_t basepos = 0;
+    if (!hm) return;
+    uint32_t basepos = 0;
+    if (kWarpSlab) {
+      basepos = wcnt;
+      wcnt += __popc(hm);
+    } else {
       const int leader = __ffs(hm) - 1;
       if (lane == leader) basepos = atomicAdd(s_cnt, (uint32_t)__popc(hm));
       basepos = __shfl_sync(0xffffffffu, basepos, leader);
-      if (hit) {
-        uint32_t t0 = inv_x, t1 = iy, t2 = a.inv[z];
-        sort3(t0, t1, t2);
-        uint32_t r = basepos + __popc(hm & lt);
-        slab[3 * r + 0] = t0;
-        slab[3 * r + 1] = t1;
-        slab[3 * r + 2] = t2;
-      }
     }
+    if (hit) {
+      // z stays a rank here; copy_out translates it off the critical path
+      const uint32_t r = basepos + __popc(hm & lt);
+      slab[3 * r + 0] = inv_x;
+      slab[3 * r + 1] = iyj;
+      slab[3 * r + 2] = z;
+    }
+  };
+  uint64_t base = i0;
+  while (base < i1) {
+    // j0 = the window's seed edge holding test `base` (32: window exhausted)
+    const int j0 = __popc(__ballot_sync(0xffffffffu, E <= base));
+    if (j0 == 32) {
+      k += 32;
+      load_window(k);
+      continue;
+    }
+    const uint64_t Ej0 = shfl_u64(E, j0);
+    if (Ej0 - base >= 32) {
+      // Long run: every test up to min(Ej0, i1) scans the same list N+_y.
+      const uint64_t Aj = shfl_u64(A, j0) + base;
+      const uint32_t iyj = __shfl_sync(0xffffffffu, iy, j0);
+      const uint64_t run = (Ej0 < i1 ? Ej0 : i1) - base;
+      for (uint64_t r = 0; r < run; r += 128) {
+        uint32_t z[4];
+        bool act[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const uint64_t o = r + 32 * u + lane;
+          act[u] = o < run;
+          z[u] = act[u] ? a.out_adj[Aj + o] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const bool h = act[u] && member(z[u]);
+          probes += act[u] ? 1 : 0;
+          emit(h, iyj, z[u]);
+        }
+      }
+      base += run;
+      continue;
+    }
+    // Short segments: one step of up to 32 tests spread over several lists.
+    uint64_t lim = base + 32;
+    if (lim > i1) lim = i1;
+    if (lim > Elast) lim = Elast;
+    const uint32_t off = lane;
+    const bool act = base + off < lim;
+    // segment ends relative to base, clamped to [0, 64]
+    const uint32_t D = (E <= base) ? 0u : (uint32_t)((E - base) < 64 ? (E - base) : 64);
+    const int j = warp_count_le(D, off);  // seed edge of test base + lane (< 32 when act)
+    const int jj = j < 31 ? j : 31;
+    const uint64_t Aj = shfl_u64(A, jj);
+    const uint32_t iyj = __shfl_sync(0xffffffffu, iy, jj);
+    bool hit = false;
+    uint32_t z = 0;
+    if (act) {
+      z = a.out_adj[Aj + base + off];
+      ++probes;
+      hit = member(z);
+    }
+    emit(hit, iyj, z);
+    base = lim;
   }
 }
 
-__device__ __forceinline__ uint64_t lower_bound_u64(const uint64_t *v, uint64_t n, uint64_t key) {
-  uint64_t lo = 0, hi = n;
-  while (lo < hi) {
-    uint64_t mid = (lo + hi) >> 1;
-    if (v[mid] < key) lo = mid + 1; else hi = mid;
-  }
-  return lo;
-}
+// ---- small and medium vertices: one warp per x, B = per-warp hash ----------
 
-__device__ __forceinline__ uint64_t upper_bound_u64(const uint64_t *v, uint64_t n, uint64_t key) {
-  uint64_t lo = 0, hi = n;
-  while (lo < hi) {
-    uint64_t mid = (lo + hi) >> 1;
-    if (v[mid] <= key) lo = mid + 1; else hi = mid;
-  }
-  return lo;
-}
-
-__global__ void __launch_bounds__(kSmallThreads) k_list_small(ListArgs a) {
-  __shared__ int64_t s_t;
-  __shared__ uint32_t s_x0, s_x1, s_next, s_cnt, s_ok;
-  __shared__ unsigned long long s_pos, s_probes;
-  uint32_t *slab = a.slabs + (uint64_t)blockIdx.x * a.slab_cap * 3;
-  const int lane = threadIdx.x & 31;
+template <int SLOTS>
+__global__ void __launch_bounds__(kWarpThreads, 4) k_list_warp(ListArgs a) {
+  extern __shared__ uint32_t sm[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t *H = sm + wid * SLOTS;
+  const uint64_t gwarp = (uint64_t)blockIdx.x * (kWarpThreads / 32) + wid;
+  uint32_t *slab = a.slabs + gwarp * a.slab_cap * 3;
   for (;;) {
-    if (threadIdx.x == 0) {
-      int64_t t = fetch_task(a.ctl, a);
-      s_t = t;
-      if (t >= 0) {
-        // task t covers the small x whose work prefix lies in [t, t+1) * kSmallWork
-        const uint64_t nr = a.x_end - a.x_begin;
-        uint64_t r0 = lower_bound_u64(a.small_prefix, nr + 1, (uint64_t)t * kSmallWork);
-        uint64_t r1 = lower_bound_u64(a.small_prefix, nr + 1, (uint64_t)(t + 1) * kSmallWork);
-        s_x0 = a.x_begin + (uint32_t)(r0 < nr ? r0 : nr);
-        s_x1 = a.x_begin + (uint32_t)(r1 < nr ? r1 : nr);
-        s_next = s_x0;
-        s_cnt = 0;
-        s_probes = 0;
-      }
-    }
-    __syncthreads();
-    const int64_t t = s_t;
+    int64_t t = 0;
+    if (lane == 0) t = fetch_task(a.ctl, a);
+    t = __shfl_sync(0xffffffffu, (long long)t, 0);
     if (t < 0) break;
-    const uint32_t x1 = s_x1;
+    const uint32_t i0 = a.task_start[t], i1 = a.task_start[t + 1];
     unsigned long long probes = 0;
-    for (;;) {
-      uint32_t x = 0;
-      if (lane == 0) x = atomicAdd(&s_next, 1u);
-      x = __shfl_sync(0xffffffffu, x, 0);
-      if (x >= x1) break;
-      const uint64_t r = x - a.x_begin;
-      if (a.small_prefix[r + 1] == a.small_prefix[r]) continue;  // not small (or no work)
-      list_small_x(a, x, slab, &s_cnt, probes);
+    uint32_t cnt = 0;
+    for (uint32_t idx = i0; idx < i1; ++idx) {
+      const uint32_t x = a.tier_x[idx];
+      const uint64_t pb = a.poff[x], pe = a.poff[x + 1];
+      const uint32_t p = (uint32_t)(pe - pb);
+      int lg = 6;
+      while ((1u << lg) < 2 * p) ++lg;  // 2p <= SLOTS by the tier's definition
+      const uint32_t cap = 1u << lg;
+      for (uint32_t i = lane; i < cap; i += 32) H[i] = kEmpty;
+      __syncwarp();
+      for (uint64_t q = pb + lane; q < pe; q += 32) hash_insert(H, lg, a.padj[q]);
+      __syncwarp();
+      scan_items<true>(a, pb, pe, pb, a.WP[pb], a.WP[pe], a.inv[x],
+                       [&](uint32_t z) { return hash_find(H, lg, z); }, slab, nullptr, cnt,
+                       probes);
+      __syncwarp();
     }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) probes += __shfl_down_sync(0xffffffffu, probes, d);
-    if (lane == 0) atomicAdd(&s_probes, probes);
-    __syncthreads();
-    commit_task(a.ctl, a, t, slab, s_cnt, s_probes, &s_ok, &s_pos);
+    commit_warp(a.ctl, a, t, slab, cnt, probes);
   }
 }
 
-// ---- large vertices: one CTA per piece, P_x in shared memory -----------------
+// ---- mid and large vertices: one CTA per piece, B shared by the CTA -------
+//   TIER 2 (mid, p <= 2048): open-addressing hash of <= 4096 slots.
+//   TIER 3 (large): a bitmap over all ranks when n <= kBitmapMaxN, else a
+//   hash of <= kHashMaxSlots slots, else binary search in the sorted row.
 
-__device__ __forceinline__ uint32_t hash_slot(uint32_t r, uint32_t mask) {
-  return (r * 0x9E3779B1u) & mask;
-}
-
-__global__ void __launch_bounds__(kLargeThreads, 1) k_list_large(ListArgs a) {
+template <int THREADS, int TIER>
+__global__ void __launch_bounds__(THREADS, TIER == 3 ? 1 : 2) k_list_cta(ListArgs a) {
   extern __shared__ uint32_t sm[];  // bitmap or hash table
   __shared__ int64_t s_t;
-  __shared__ uint32_t s_x, s_cnt, s_ok, s_mode, s_mask;
+  __shared__ uint32_t s_x, s_cnt, s_ok, s_mode, s_lg;
   __shared__ unsigned long long s_pos, s_probes, s_a, s_b;
-  __shared__ uint64_t s_k0;
   uint32_t *slab = a.slabs + (uint64_t)blockIdx.x * a.slab_cap * 3;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int nwarps = blockDim.x >> 5;
-  const bool use_bitmap = a.n <= kBitmapMaxN;
+  constexpr int kWarps = THREADS / 32;
+  const bool use_bitmap = TIER == 3 && a.n <= kBitmapMaxN;
   if (use_bitmap) {
     const uint32_t words = (a.n + 31) >> 5;
-    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) sm[i] = 0;
+    for (uint32_t i = threadIdx.x; i < words; i += THREADS) sm[i] = 0;
   }
-  const unsigned lt = (1u << lane) - 1u;
   for (;;) {
     if (threadIdx.x == 0) {
-      int64_t t = fetch_task(a.ctl, a);
+      const int64_t t = fetch_task(a.ctl, a);
       s_t = t;
       if (t >= 0) {
         // x = the vertex whose piece range contains t
         const uint64_t nr = a.x_end - a.x_begin;
-        uint64_t r = upper_bound_u64(a.piece_prefix, nr + 1, (uint64_t)t) - 1;
+        const uint64_t r = upper_bound_u64(a.piece_prefix, nr + 1, (uint64_t)t) - 1;
         const uint32_t x = a.x_begin + (uint32_t)r;
         const uint64_t piece = (uint64_t)t - a.piece_prefix[r];
         const uint64_t pb = a.poff[x], pe = a.poff[x + 1];
+        const uint64_t p = pe - pb;
         const uint64_t w0 = a.WP[pb], w1 = a.WP[pe];
-        const uint64_t ia = w0 + piece * kPieceWork;
-        const uint64_t ib = (ia + kPieceWork < w1) ? ia + kPieceWork : w1;
+        const uint64_t pw = piece_work(TIER, p);
+        const uint64_t ia = w0 + piece * pw;
         s_x = x;
         s_a = ia;
-        s_b = ib;
-        // first seed edge whose item range reaches past ia
-        s_k0 = pb + upper_bound_u64(a.WP + pb, pe - pb, ia) - 1;
+        s_b = (ia + pw < w1) ? ia + pw : w1;
         s_cnt = 0;
         s_probes = 0;
-        const uint64_t p = pe - pb;
+        s_lg = 6;
         if (use_bitmap) {
           s_mode = 0;
         } else {
-          uint32_t cap = 64;
-          while (cap < 2 * p && cap < kHashMaxSlots) cap <<= 1;
-          if (2 * p <= cap) {
-            s_mode = 1;
-            s_mask = cap - 1;
-          } else {
-            s_mode = 2;  // probe set too large for shared memory: binary search
-          }
+          const uint32_t max_slots = TIER == 2 ? (uint32_t)kMidSlots : kHashMaxSlots;
+          uint32_t lg = 6;
+          while ((1ull << lg) < 2 * p && (1u << lg) < max_slots) ++lg;
+          s_lg = lg;
+          s_mode = (2 * p <= (1ull << lg)) ? 1 : 2;  // 2: too large, binary search
         }
       }
     }
@@ -276,86 +400,56 @@ __global__ void __launch_bounds__(kLargeThreads, 1) k_list_large(ListArgs a) {
     if (t < 0) break;
     const uint32_t x = s_x;
     const uint64_t pb = a.poff[x], pe = a.poff[x + 1];
-    const uint32_t mode = s_mode, mask = s_mask;
+    const uint32_t mode = s_mode;
+    const int lg = (int)s_lg;
     // build B: the probe set P_x
     if (mode == 0) {
-      for (uint64_t k = pb + threadIdx.x; k < pe; k += blockDim.x) {
-        uint32_t r = a.padj[k];
+      for (uint64_t q = pb + threadIdx.x; q < pe; q += THREADS) {
+        const uint32_t r = a.padj[q];
         atomicOr(&sm[r >> 5], 1u << (r & 31));
       }
     } else if (mode == 1) {
-      for (uint32_t i = threadIdx.x; i <= mask; i += blockDim.x) sm[i] = kNone;
+      for (uint32_t i = threadIdx.x; i < (1u << lg); i += THREADS) sm[i] = kEmpty;
       __syncthreads();
-      for (uint64_t k = pb + threadIdx.x; k < pe; k += blockDim.x) {
-        uint32_t r = a.padj[k];
-        uint32_t h = hash_slot(r, mask);
-        while (atomicCAS(&sm[h], kNone, r) != kNone) h = (h + 1) & mask;
-      }
+      for (uint64_t q = pb + threadIdx.x; q < pe; q += THREADS) hash_insert(sm, lg, a.padj[q]);
     }
     __syncthreads();
+    // the piece's tests, split into one contiguous range per warp
     const uint64_t ia = s_a, ib = s_b;
+    const uint64_t per = (((ib - ia) + kWarps - 1) / kWarps + 31) & ~31ull;
+    uint64_t wa = ia + (uint64_t)wid * per;
+    uint64_t wb = wa + per;
+    if (wa > ib) wa = ib;
+    if (wb > ib) wb = ib;
     const uint32_t inv_x = a.inv[x];
     unsigned long long probes = 0;
-    for (uint64_t k = s_k0 + wid; k < pe; k += nwarps) {
-      const uint64_t wk = a.WP[k];
-      if (wk >= ib) break;
-      const uint64_t wk1 = a.WP[k + 1];
-      const uint32_t y = a.padj[k];
-      const uint64_t st = a.out_off[y];
-      const uint64_t lo = (ia > wk ? ia : wk) - wk;
-      const uint64_t hi = (ib < wk1 ? ib : wk1) - wk;
-      const uint32_t iy = a.inv[y];
-      for (uint64_t base = lo; base < hi; base += 32) {
-        const uint64_t pos = base + lane;
-        const bool act = pos < hi;
-        bool hit = false;
-        uint32_t z = 0;
-        if (act) {
-          z = a.out_adj[st + pos];
-          ++probes;
-          if (mode == 0) {
-            hit = (sm[z >> 5] >> (z & 31)) & 1u;
-          } else if (mode == 1) {
-            uint32_t h = hash_slot(z, mask);
-            for (;;) {
-              uint32_t v = sm[h];
-              if (v == z) { hit = true; break; }
-              if (v == kNone) break;
-              h = (h + 1) & mask;
-            }
-          } else {
-            uint64_t lo2 = pb, hi2 = pe;
-            while (lo2 < hi2) {
-              uint64_t mid = (lo2 + hi2) >> 1;
-              if (a.padj[mid] < z) lo2 = mid + 1; else hi2 = mid;
-            }
-            hit = lo2 < pe && a.padj[lo2] == z;
-          }
-        }
-        const unsigned hm = __ballot_sync(0xffffffffu, hit);
-        if (hm) {
-          uint32_t basepos = 0;
-          const int leader = __ffs(hm) - 1;
-          if (lane == leader) basepos = atomicAdd(&s_cnt, (uint32_t)__popc(hm));
-          basepos = __shfl_sync(0xffffffffu, basepos, leader);
-          if (hit) {
-            uint32_t t0 = inv_x, t1 = iy, t2 = a.inv[z];
-            sort3(t0, t1, t2);
-            uint32_t r = basepos + __popc(hm & lt);
-            slab[3 * r + 0] = t0;
-            slab[3 * r + 1] = t1;
-            slab[3 * r + 2] = t2;
-          }
-        }
-      }
+    uint32_t unused = 0;
+    if (mode == 0) {
+      scan_items<false>(a, pb, pe, ~0ull, wa, wb, inv_x,
+                        [&](uint32_t z) { return ((sm[z >> 5] >> (z & 31)) & 1u) != 0; }, slab,
+                        &s_cnt, unused, probes);
+    } else if (mode == 1) {
+      scan_items<false>(a, pb, pe, ~0ull, wa, wb, inv_x,
+                        [&](uint32_t z) { return hash_find(sm, lg, z); }, slab, &s_cnt, unused,
+                        probes);
+    } else {
+      scan_items<false>(a, pb, pe, ~0ull, wa, wb, inv_x,
+                        [&](uint32_t z) {
+                          uint64_t lo = pb, hi = pe;
+                          while (lo < hi) {
+                            const uint64_t mid = (lo + hi) >> 1;
+                            if (a.padj[mid] < z) lo = mid + 1; else hi = mid;
+                          }
+                          return lo < pe && a.padj[lo] == z;
+                        },
+                        slab, &s_cnt, unused, probes);
     }
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) probes += __shfl_down_sync(0xffffffffu, probes, d);
     if (lane == 0) atomicAdd(&s_probes, probes);
     __syncthreads();
-    // reset B
-    if (mode == 0) {
-      for (uint64_t k = pb + threadIdx.x; k < pe; k += blockDim.x) sm[a.padj[k] >> 5] = 0;
+    if (mode == 0) {  // reset B
+      for (uint64_t q = pb + threadIdx.x; q < pe; q += THREADS) sm[a.padj[q] >> 5] = 0;
     }
     commit_task(a.ctl, a, t, slab, s_cnt, s_probes, &s_ok, &s_pos);
   }
@@ -368,16 +462,16 @@ __global__ void k_seed_work(const uint32_t *__restrict__ padj, uint64_t m,
                             const uint64_t *__restrict__ out_off, uint32_t *__restrict__ w) {
   for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < m;
        k += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t y = padj[k];
+    const uint32_t y = padj[k];
     w[k] = (uint32_t)(out_off[y + 1] - out_off[y]);
   }
 }
 
-// Per x in the range: small work (W_x if small, else 0) and piece count (if
-// large, else 0).
 __global__ void k_classify(const uint64_t *__restrict__ poff, const uint64_t *__restrict__ WP,
-                           uint32_t x_begin, uint32_t x_end, uint64_t *__restrict__ small_w,
-                           uint64_t *__restrict__ pieces) {
+                           uint32_t x_begin, uint32_t x_end, uint64_t *__restrict__ w0,
+                           uint64_t *__restrict__ w1, uint32_t *__restrict__ f0,
+                           uint32_t *__restrict__ f1, uint64_t *__restrict__ pieces2,
+                           uint64_t *__restrict__ pieces3) {
   const uint64_t nr = x_end - x_begin;
   for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < nr;
        r += (uint64_t)gridDim.x * blockDim.x) {
@@ -385,15 +479,46 @@ __global__ void k_classify(const uint64_t *__restrict__ poff, const uint64_t *__
     const uint64_t pb = poff[x], pe = poff[x + 1];
     const uint64_t W = WP[pe] - WP[pb];
     const uint64_t p = pe - pb;
-    uint64_t sw = 0, np = 0;
+    uint64_t a0 = 0, a1 = 0, n2 = 0, n3 = 0;
     if (p > 0 && W > 0) {
-      if (p <= 32 && W <= kSmallWork)
-        sw = W;
+      if (p <= kSmallMaxP && W <= kWarpWork)
+        a0 = W + kVertexCost;
+      else if (p <= kMediumMaxP && W <= kWarpWork)
+        a1 = W + kVertexCost;
+      else if (p <= kMidMaxP)
+        n2 = (W + piece_work(2, p) - 1) / piece_work(2, p);
       else
-        np = (W + kPieceWork - 1) / kPieceWork;
+        n3 = (W + piece_work(3, p) - 1) / piece_work(3, p);
     }
-    small_w[r] = sw;
-    pieces[r] = np;
+    w0[r] = a0;
+    w1[r] = a1;
+    f0[r] = a0 ? 1u : 0u;
+    f1[r] = a1 ? 1u : 0u;
+    pieces2[r] = n2;
+    pieces3[r] = n3;
+  }
+}
+
+__global__ void k_compact_tier(const uint32_t *__restrict__ flags, const uint64_t *__restrict__ pos,
+                               const uint64_t *__restrict__ pref, uint32_t x_begin, uint64_t nr,
+                               uint32_t *__restrict__ x_list, uint64_t *__restrict__ wp_list) {
+  for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r <= nr;
+       r += (uint64_t)gridDim.x * blockDim.x) {
+    if (r == nr) {
+      wp_list[pos[nr]] = pref[nr];  // total work after the last vertex
+    } else if (flags[r]) {
+      x_list[pos[r]] = x_begin + (uint32_t)r;
+      wp_list[pos[r]] = pref[r];
+    }
+  }
+}
+
+__global__ void k_task_bounds(const uint64_t *__restrict__ wp, uint64_t count, uint64_t n_tasks,
+                              uint32_t *__restrict__ task_start) {
+  for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t <= n_tasks;
+       t += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t i = lower_bound_u64(wp, count + 1, t * kWarpWork);
+    task_start[t] = (uint32_t)(i < count ? i : count);
   }
 }
 
@@ -421,6 +546,19 @@ __global__ void k_count_hash(const uint32_t *__restrict__ t, uint64_t n,
   if ((threadIdx.x & 31) == 0) atomicAdd(acc, h);
 }
 
+template <class K>
+int occupancy_grid(K kernel, int threads, int smem) {
+  if (smem > 48 * 1024)
+    TL_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  int per_sm = 0;
+  TL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem));
+  return num_sms() * (per_sm > 0 ? per_sm : 1);
+}
+
+constexpr int kSmemSmall = kSmallSlots * 4 * (kWarpThreads / 32);
+constexpr int kSmemMedium = kMediumSlots * 4 * (kWarpThreads / 32);
+constexpr int kSmemMid = kMidSlots * 4;
+
 }  // namespace
 
 // ---- host side ----------------------------------------------------------------
@@ -432,41 +570,49 @@ void launch_seed_work(const uint32_t *padj, uint64_t m, const uint64_t *out_off,
 }
 
 void launch_classify(const uint64_t *poff, const uint64_t *WP, uint32_t x_begin, uint32_t x_end,
-                     uint64_t *small_w, uint64_t *pieces, cudaStream_t s) {
-  k_classify<<<grid_for((uint64_t)(x_end - x_begin), 256), 256, 0, s>>>(poff, WP, x_begin, x_end,
-                                                                        small_w, pieces);
+                     uint64_t *w0, uint64_t *w1, uint32_t *f0, uint32_t *f1, uint64_t *pieces2,
+                     uint64_t *pieces3, cudaStream_t s) {
+  k_classify<<<grid_for((uint64_t)(x_end - x_begin), 256), 256, 0, s>>>(
+      poff, WP, x_begin, x_end, w0, w1, f0, f1, pieces2, pieces3);
   TL_CHECK_LAUNCH();
 }
 
-int small_grid() {
-  static int g = 0;
-  if (!g) {
-    int per_sm = 0;
-    TL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_list_small, kSmallThreads, 0));
-    g = num_sms() * (per_sm > 0 ? per_sm : 1);
-  }
-  return g;
+void launch_compact_tier(const uint32_t *flags, const uint64_t *pos, const uint64_t *pref,
+                         uint32_t x_begin, uint64_t nr, uint32_t *x_list, uint64_t *wp_list,
+                         cudaStream_t s) {
+  k_compact_tier<<<grid_for(nr + 1, 256), 256, 0, s>>>(flags, pos, pref, x_begin, nr, x_list,
+                                                       wp_list);
+  TL_CHECK_LAUNCH();
 }
 
-int large_grid() {
-  static int g = 0;
-  if (!g) {
-    TL_CUDA(cudaFuncSetAttribute(k_list_large, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kLargeSmemBytes));
-    int per_sm = 0;
-    TL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_list_large, kLargeThreads,
-                                                          kLargeSmemBytes));
-    g = num_sms() * (per_sm > 0 ? per_sm : 1);
-  }
-  return g;
+void launch_task_bounds(const uint64_t *wp_list, uint64_t count, uint64_t n_tasks,
+                        uint32_t *task_start, cudaStream_t s) {
+  k_task_bounds<<<grid_for(n_tasks + 1, 256), 256, 0, s>>>(wp_list, count, n_tasks, task_start);
+  TL_CHECK_LAUNCH();
 }
 
-void launch_list(int kind, const ListArgs &a, cudaStream_t s) {
-  if (kind == 0) {
-    k_list_small<<<small_grid(), kSmallThreads, 0, s>>>(a);
+int tier_grid(int tier) {
+  static int g[kTiers] = {0, 0, 0, 0};
+  if (!g[tier]) {
+    if (tier == 0) g[0] = occupancy_grid(k_list_warp<kSmallSlots>, kWarpThreads, kSmemSmall);
+    if (tier == 1) g[1] = occupancy_grid(k_list_warp<kMediumSlots>, kWarpThreads, kSmemMedium);
+    if (tier == 2) g[2] = occupancy_grid(k_list_cta<kMidThreads, 2>, kMidThreads, kSmemMid);
+    if (tier == 3)
+      g[3] = occupancy_grid(k_list_cta<kLargeThreads, 3>, kLargeThreads, kLargeSmemBytes);
+  }
+  return g[tier];
+}
+
+void launch_list(int tier, const ListArgs &a, cudaStream_t s) {
+  const int grid = tier_grid(tier);
+  if (tier == 0) {
+    k_list_warp<kSmallSlots><<<grid, kWarpThreads, kSmemSmall, s>>>(a);
+  } else if (tier == 1) {
+    k_list_warp<kMediumSlots><<<grid, kWarpThreads, kSmemMedium, s>>>(a);
+  } else if (tier == 2) {
+    k_list_cta<kMidThreads, 2><<<grid, kMidThreads, kSmemMid, s>>>(a);
   } else {
-    large_grid();
-    k_list_large<<<large_grid(), kLargeThreads, kLargeSmemBytes, s>>>(a);
+    k_list_cta<kLargeThreads, 3><<<grid, kLargeThreads, kLargeSmemBytes, s>>>(a);
   }
   TL_CHECK_LAUNCH();
 }

@@ -5,19 +5,48 @@
 
 namespace tl {
 
-constexpr int kSmallThreads = 256;
+// Tiers of B vertices x (by probe-set size p = |P_x| and work W_x):
+//   0 small:  p <= 32,   W <= kWarpWork  -- one warp per x, 64-slot hash per warp
+//   1 medium: p <= 1024, W <= kWarpWork  -- one warp per x, 2048-slot hash per warp
+//   2 mid:    p <= 2048, W >  kWarpWork  -- 256-thread CTA per piece, 4096-slot hash
+//   3 large:  p >  2048                  -- 1024-thread CTA per piece, bitmap / hash
+constexpr int kTiers = 4;
+constexpr int kWarpThreads = 256;
+constexpr int kMidThreads = 256;
 constexpr int kLargeThreads = 1024;
-// Work (membership tests) of one task: a small task groups small vertices
-// up to about kSmallWork tests (at most 2 * kSmallWork); a large vertex is
-// cut into pieces of at most kPieceWork tests.
-constexpr uint64_t kSmallWork = 1u << 16;
+constexpr uint32_t kSmallMaxP = 32, kMediumMaxP = 1024, kMidMaxP = 2048;
+constexpr int kSmallSlots = 64, kMediumSlots = 2048;  // per warp, >= 2p (load <= 1/2)
+constexpr int kMidSlots = 4096;                        // per CTA, >= 2p
+// Work (membership tests) per task: a warp-tier task is owned by one warp
+// and groups vertices up to about kWarpWork units, a vertex weighing its
+// tests plus kVertexCost (its setup is a chain of dependent loads); each
+// vertex has <= kWarpWork tests, so a task has < 2 kWarpWork tests.  A
+// mid or large vertex is cut into pieces of piece_work(tier, p) tests
+// shared by a CTA.
+constexpr uint64_t kWarpWork = 1u << 12;
+constexpr uint64_t kVertexCost = 256;
+constexpr uint64_t kMidPiece = 1u << 15;
 constexpr uint64_t kPieceWork = 1u << 16;
+constexpr uint64_t kPieceMax = 1u << 18;
+__host__ __device__ inline uint64_t piece_work(int tier, uint64_t p) {
+  if (tier == 2) return kMidPiece;
+  uint64_t w = 4 * p;
+  w = w < kPieceWork ? kPieceWork : w;
+  return w > kPieceMax ? kPieceMax : w;
+}
 // Shared-memory probe structures of the large kernel.
-constexpr uint32_t kBitmapMaxN = 1572864u;              // 192 KiB bitmap over ranks
-constexpr uint32_t kHashMaxSlots = 32768u;              // 128 KiB hash table
+constexpr uint32_t kBitmapMaxN = 1572864u;               // 192 KiB bitmap over ranks
+constexpr uint32_t kHashMaxSlots = 32768u;               // 128 KiB hash table
 constexpr int kLargeSmemBytes = (int)(kBitmapMaxN / 8);  // >= kHashMaxSlots * 4
-// Triangles a task can produce (bounded by its work).
-constexpr uint64_t kSlabCap = 2 * kSmallWork > kPieceWork ? 2 * kSmallWork : kPieceWork;
+// Triangles a task can produce (bounded by its work): per warp for the warp
+// tiers, per CTA for the mid and large tiers.
+constexpr uint64_t kSlabCapWarp = 2 * kWarpWork;
+constexpr uint64_t kSlabCapMid = kMidPiece;
+constexpr uint64_t kSlabCapLarge = kPieceMax;
+constexpr uint64_t kSlabCap = kSlabCapLarge;
+__host__ __device__ inline uint64_t slab_cap(int tier) {
+  return tier < 2 ? kSlabCapWarp : (tier == 2 ? kSlabCapMid : kSlabCapLarge);
+}
 
 // Device control block of one listing launch.
 struct ListCtl {
@@ -39,8 +68,15 @@ struct ListArgs {
   const uint32_t *out_adj;
   const uint32_t *inv;           // rank -> original id
   const uint64_t *WP;            // work prefix over probe-side entries [m+1]
-  const uint64_t *small_prefix;  // over x in range [nr+1]
-  const uint64_t *piece_prefix;  // over x in range [nr+1]
+  // warp tiers: the tier's vertices in rank order and their work prefix
+  // [count+1]; task t holds vertices [task_start[t], task_start[t+1])
+  const uint32_t *tier_x;
+  const uint64_t *tier_wp;
+  const uint32_t *task_start;
+  uint64_t tier_count;
+  // mid / large tier: piece prefix over x in [x_begin, x_end) [nr+1]
+  const uint64_t *piece_prefix;
+  int tier;
   ListCtl *ctl;
   uint32_t *chunk;               // output chunk, 3 uint32 per triangle
   uint64_t chunk_cap;            // triangles
@@ -55,12 +91,22 @@ struct ListArgs {
 
 void launch_seed_work(const uint32_t *padj, uint64_t m, const uint64_t *out_off, uint32_t *w,
                       cudaStream_t s);
+// Per x in [x_begin, x_end): weight in tier 0 / 1 (0 if not in the tier),
+// the membership flags, and the piece counts of tiers 2 and 3.
 void launch_classify(const uint64_t *poff, const uint64_t *WP, uint32_t x_begin, uint32_t x_end,
-                     uint64_t *small_w, uint64_t *pieces, cudaStream_t s);
-// kind 0: small-vertex kernel, kind 1: large-vertex kernel.
-void launch_list(int kind, const ListArgs &a, cudaStream_t s);
-int small_grid();
-int large_grid();
+                     uint64_t *w0, uint64_t *w1, uint32_t *f0, uint32_t *f1, uint64_t *pieces2,
+                     uint64_t *pieces3, cudaStream_t s);
+// Compact the vertices of one warp tier: x_list[pos[r]] = x, wp_list[pos[r]] = pref[r].
+void launch_compact_tier(const uint32_t *flags, const uint64_t *pos, const uint64_t *pref,
+                         uint32_t x_begin, uint64_t nr, uint32_t *x_list, uint64_t *wp_list,
+                         cudaStream_t s);
+// task_start[t] = first tier vertex whose work prefix is >= t * kWarpWork
+// (clamped to count), t in [0, n_tasks].
+void launch_task_bounds(const uint64_t *wp_list, uint64_t count, uint64_t n_tasks,
+                        uint32_t *task_start, cudaStream_t s);
+// tier 0, 1: warp kernels; tier 2: mid CTA kernel; tier 3: large CTA kernel.
+void launch_list(int tier, const ListArgs &a, cudaStream_t s);
+int tier_grid(int tier);
 void launch_count_hash(const uint32_t *t, uint64_t n, unsigned long long *acc, cudaStream_t s);
 
 }  // namespace tl

@@ -236,6 +236,36 @@ def test_count_hash_consumer_matches_oracle():
         assert (nt, cnt, h, probes) == (rc, rc, rh, rp)
 
 
+def test_every_tier_runs_and_matches():
+    """Chung-Lu graph plus a wheel (hub joined to a 5000-cycle): probe sets of
+    every size, so all four listing kernels (small, medium, mid, large with
+    the shared-memory bitmap) get tasks; full set compare with the oracle."""
+    n = 60000
+    base = synth.chung_lu(n, 24, 2.1, 21)
+    k = 5000
+    spokes = np.stack([np.zeros(k, np.uint32), np.arange(1, k + 1, dtype=np.uint32)], 1)
+    rim = np.stack([np.arange(1, k + 1, dtype=np.uint32),
+                    np.r_[np.arange(2, k + 1), 1].astype(np.uint32)], 1)
+    e = np.concatenate([base, spokes, rim])
+    off, adj = synth.simple_csr(n, e)
+    seen = np.zeros(4, dtype=np.int64)
+    g = tl.Graph(n, _dev(e))
+    ref = oracle.Graph(n, e)
+    for name, rank in [("degree", synth.order_degree(off)), ("identity", synth.order_identity(n)),
+                       ("random", synth.order_random(n, 4))]:
+        g.order_apply(_dev(rank))
+        ref.order_apply(rank)
+        for alg in (tl.TL_APP, tl.TL_APM):
+            t, nt, probes, _ = g.list_collect(alg)
+            st = tl.tl_last_list_stats(g.h)
+            seen += np.array(st["tasks"]) > 0
+            rt, rc, rh, rp = ref.list(alg)
+            assert (nt, probes) == (rc, rp), (name, alg)
+            assert sum(st["kernel_probes"]) == rp and sum(st["kernel_triangles"]) == rc
+            assert np.array_equal(oracle.canonical(t), oracle.canonical(rt)), (name, alg)
+    assert np.all(seen > 0), seen
+
+
 def test_large_n_hash_probe_path():
     """n above the shared-memory bitmap limit (1,572,864 ranks): the large
     kernel probes with a shared-memory hash table, and with binary search for
