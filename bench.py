@@ -166,21 +166,33 @@ def run_tl(args):
     ch = tl.CountHash(stream.cuda_stream)
     ch_ptr = tl.tl_count_hash_ptr()
 
+    phase_names = ["graph_load", "order_apply", "list_A++", "list_A+-", "graph_free"]
+    phase_ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(phase_names) + 1)]
+    phase_ms = {k: [] for k in phase_names}
+
     def step(edges, ranks):
+        phase_ev[0].record(stream)
         g = tl.tl_graph_load(n, edges, stream.cuda_stream)
+        phase_ev[1].record(stream)
         try:
             tl.tl_order_apply(g, ranks)
+            phase_ev[2].record(stream)
             m = tl.tl_graph_size(g)[1]
             costs = [tl.tl_cost(g, a) for a in (tl.TL_APP, tl.TL_APM)]
             out = []
-            for a in (tl.TL_APP, tl.TL_APM):
+            for i, a in enumerate((tl.TL_APP, tl.TL_APM)):
                 ch.reset()
                 nt = tl.tl_list_triangles(g, a, CHUNK_BYTES, ch_ptr, ch.user)
+                phase_ev[3 + i].record(stream)
                 out.append((nt, int(ch.state.count), int(ch.state.hash),
                             tl.tl_last_list_stats(g)))
             return m, costs, out
         finally:
             tl.tl_graph_free(g)
+            phase_ev[5].record(stream)
+            phase_ev[5].synchronize()
+            for i, k in enumerate(phase_names):
+                phase_ms[k].append(phase_ev[i].elapsed_time(phase_ev[i + 1]))
 
     def barrier():
         torch.cuda.synchronize()
@@ -206,6 +218,7 @@ def run_tl(args):
     barrier()
     clk = clocks.stop()
     launches = tl.tl_kernel_launches() - launches0
+    timed_phase_ms = {k: statistics.median(v[-args.steps:]) for k, v in phase_ms.items()}
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
     if dist:
@@ -265,6 +278,7 @@ def run_tl(args):
                          "algorithmic_bytes_per_step": alg_bytes, "kernel_ms_per_step": list_ms,
                          "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"},
             "list_stats": {a: r[3] for a, r in zip(("A++", "A+-"), out)},
+            "phase_ms_median": timed_phase_ms,
             "gpu_launches": launches,
             "clocks": clk,
             "cpu_baseline": cpu,

@@ -1,6 +1,7 @@
 // C ABI of libtl (declared in include/tl.h).
 #include <atomic>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -16,6 +17,23 @@ std::atomic<uint64_t> g_launches{0};
 void set_error(const std::string &msg) { g_last_error = msg; }
 void clear_error() { g_last_error.clear(); }
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+cudaMemPool_t device_pool() {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  TL_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) fail(TL_EINVAL, "device index out of range");
+  std::lock_guard<std::mutex> lock(mu);
+  if (!pools[dev]) {
+    cudaMemPool_t p;
+    TL_CUDA(cudaDeviceGetDefaultMemPool(&p, dev));
+    uint64_t keep = ~0ull;
+    TL_CUDA(cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep));
+    pools[dev] = p;
+  }
+  return pools[dev];
+}
 
 namespace {
 
@@ -41,7 +59,7 @@ struct tl_graph {
   // per-vertex classification (tiers 0, 1: weights and flags; tiers 2, 3: pieces),
   // their prefixes, and the compacted vertex lists of tiers 0 and 1
   tl::DevBuf tw[2], tf[2], tpref[2], tpos[2], tx[2], twp[2], tstart[2], pieces[2],
-      piece_prefix[2];
+      piece_prefix[2], task_x[2];
   tl::PinnedCtl *pctl = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr};
   tl_list_stats stats{};
@@ -49,6 +67,14 @@ struct tl_graph {
   uint32_t cached_xb = 0, cached_xe = 0;
   uint64_t n_tasks[tl::kTiers] = {0, 0, 0, 0};
   uint64_t tier_count[2] = {0, 0};
+  void bind(cudaStream_t s) {
+    g.bind(s);
+    for (tl::DevBuf *b : {&wseed, &WP, &ctl, &chunks, &slabs, &retry}) b->stream = s;
+    for (int t = 0; t < 2; ++t)
+      for (tl::DevBuf *b : {&tw[t], &tf[t], &tpref[t], &tpos[t], &tx[t], &twp[t], &tstart[t],
+                            &pieces[t], &piece_prefix[t], &task_x[t]})
+        b->stream = s;
+  }
   ~tl_graph() {
     delete pctl;
     for (auto &e : ev)
@@ -147,6 +173,9 @@ void bucketize(tl_graph *G, int alg, uint32_t xb, uint32_t xe) {
     G->tstart[t].reserve((G->n_tasks[t] + 1) * 4);
     tl::launch_task_bounds(G->twp[t].as<uint64_t>(), G->tier_count[t], G->n_tasks[t],
                            G->tstart[t].as<uint32_t>(), s);
+    G->task_x[t].reserve((G->n_tasks[2 + t] ? G->n_tasks[2 + t] : 1) * 4);
+    tl::launch_task_owner(G->piece_prefix[t].as<uint64_t>(), xb, nr, G->task_x[t].as<uint32_t>(),
+                          s);
   }
   G->cached_alg = alg;
   G->cached_xb = xb;
@@ -245,7 +274,10 @@ tl_status list_impl(tl_graph *G, int alg, uint32_t xb, uint32_t xe, size_t chunk
       a.n_tasks = P->n_tasks;
       a.slab_cap = tl::slab_cap(P->kind);
       a.tier = P->kind;
-      if (P->kind >= 2) a.piece_prefix = G->piece_prefix[P->kind - 2].as<uint64_t>();
+      if (P->kind >= 2) {
+        a.piece_prefix = G->piece_prefix[P->kind - 2].as<uint64_t>();
+        a.task_x = G->task_x[P->kind - 2].as<uint32_t>();
+      }
       if (P->kind < 2) {
         a.tier_x = G->tx[P->kind].as<uint32_t>();
         a.tier_wp = G->twp[P->kind].as<uint64_t>();
@@ -325,16 +357,18 @@ tl_status tl_graph_load(tl_graph **out, uint32_t n, const uint32_t *edges, uint6
   tl_graph *G = new tl_graph();
   try {
     G->g.n = n;
-    G->g.stream = static_cast<cudaStream_t>(stream);
+    G->bind(static_cast<cudaStream_t>(stream));
     tl::build_edge_set(G->g, edges, m_in, edges_on_device != 0);
     // identity ordering (the dataset's original ordering)
-    tl::DevBuf ident;
+    tl::DevBuf ident(G->g.stream);
     ident.reserve((uint64_t)n * 4);
     {
       uint32_t *h = nullptr;
       TL_CUDA(cudaMallocHost(&h, (uint64_t)n * 4));
       for (uint32_t v = 0; v < n; ++v) h[v] = v;
-      cudaError_t e = cudaMemcpy(ident.p, h, (uint64_t)n * 4, cudaMemcpyHostToDevice);
+      cudaError_t e = cudaMemcpyAsync(ident.p, h, (uint64_t)n * 4, cudaMemcpyHostToDevice,
+                                      G->g.stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(G->g.stream);
       cudaFreeHost(h);
       TL_CUDA(e);
     }

@@ -167,7 +167,7 @@ void build_edge_set(DeviceGraph &g, const uint32_t *edges, uint64_t m_in, bool o
     return;
   }
   const uint32_t *dev_edges = edges;
-  DevBuf staged;
+  DevBuf staged(s);
   if (!on_device) {
     staged.reserve(m_in * 8);
     TL_CUDA(cudaMemcpyAsync(staged.p, edges, m_in * 8, cudaMemcpyHostToDevice, s));
@@ -183,7 +183,7 @@ void build_edge_set(DeviceGraph &g, const uint32_t *edges, uint64_t m_in, bool o
   const int b = bits_for(n > 1 ? n - 1 : 1);
   radix_sort_u64(ka, kb, m_in, 0, b, 32, b, g.sort_tmp, g.scan_tmp, s);
   // unique (flags in kb's storage as uint32, positions after them)
-  DevBuf pos;
+  DevBuf pos(s);
   pos.reserve((m_in + 1) * 8);
   uint32_t *flags = reinterpret_cast<uint32_t *>(kb);
   k_unique_flags<<<grid_for(m_in, kThreads), kThreads, 0, s>>>(ka, m_in, flags);
@@ -208,7 +208,7 @@ void build_dag(DeviceGraph &g, const uint32_t *rank, bool on_device) {
   TL_CUDA(cudaMemsetAsync(g.small.p, 0, 256, s));
 
   // a2: the ordering must be a permutation of [0, n).
-  DevBuf rank_new, cnt;
+  DevBuf rank_new(s), cnt(s);
   rank_new.reserve((uint64_t)n * 4);
   TL_CUDA(cudaMemcpyAsync(rank_new.p, rank, (uint64_t)n * 4,
                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
@@ -231,7 +231,9 @@ void build_dag(DeviceGraph &g, const uint32_t *rank, bool on_device) {
 
   g.out_off.reserve(((uint64_t)n + 1) * 8);
   g.in_off.reserve(((uint64_t)n + 1) * 8);
-  g.out_adj.reserve((m ? m : 1) * 4);
+  // +4 elements: the listing kernels read N+ lists with aligned 16-byte loads
+  // that may extend up to 3 elements past the last list.
+  g.out_adj.reserve((m + 4) * 4);
   g.in_adj.reserve((m ? m : 1) * 4);
   if (m > 0) {
     // a3: relabel + orient.

@@ -42,17 +42,26 @@ void count_launch();
 
 inline void fail(tl_status s, const std::string &msg) { throw Error{s, msg}; }
 
-// ---- device buffer (RAII over cudaMalloc) -----------------------------------
+// ---- device buffer (RAII, stream-ordered) ------------------------------------
 
+// The current device's default memory pool, set once per device to keep
+// freed memory cached (release threshold = unlimited) so that buffers of
+// repeated calls are recycled without driver round trips.
+cudaMemPool_t device_pool();
+
+// Allocations come from the device pool in stream order on `stream` (the
+// owning graph's stream; it must outlive the buffer).
 struct DevBuf {
   void *p = nullptr;
   size_t bytes = 0;
+  cudaStream_t stream = nullptr;
   DevBuf() = default;
+  explicit DevBuf(cudaStream_t s) : stream(s) {}
   DevBuf(const DevBuf &) = delete;
   DevBuf &operator=(const DevBuf &) = delete;
   ~DevBuf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, stream);
     p = nullptr;
     bytes = 0;
   }
@@ -61,7 +70,7 @@ struct DevBuf {
     if (b <= bytes && p) return;
     release();
     size_t want = b ? b : 16;
-    TL_CUDA(cudaMalloc(&p, want));
+    TL_CUDA(cudaMallocFromPoolAsync(&p, want, device_pool(), stream));
     bytes = want;
   }
   template <class T> T *as() const { return static_cast<T *>(p); }

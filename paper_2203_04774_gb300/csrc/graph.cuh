@@ -20,6 +20,13 @@ struct DeviceGraph {
   DevBuf keys_a, keys_b, sort_tmp, scan_tmp, small;  // small: flags/counters
   uint64_t cost_app = 0, cost_apm = 0;
   uint32_t max_out_deg = 0, max_in_deg = 0;
+  // Order every buffer's allocation and release on stream s.
+  void bind(cudaStream_t s) {
+    stream = s;
+    for (DevBuf *b : {&E, &rank, &inv, &out_off, &out_adj, &in_off, &in_adj, &keys_a, &keys_b,
+                      &sort_tmp, &scan_tmp, &small})
+      b->stream = s;
+  }
 };
 
 // a1: copy + canonicalise + dedup (build.cu).  Throws tl::Error.

@@ -118,12 +118,31 @@ __device__ __forceinline__ int64_t fetch_task(ListCtl *ctl, const ListArgs &a) {
 // where all gathers of the task are independent.
 __device__ __forceinline__ void copy_out(const ListArgs &a, const uint32_t *slab, uint32_t cnt,
                                          uint32_t *dst, uint32_t tid, uint32_t nthreads) {
-  for (uint32_t i = tid; i < cnt; i += nthreads) {
-    uint32_t t0 = slab[3 * i], t1 = slab[3 * i + 1], t2 = a.inv[slab[3 * i + 2]];
-    sort3(t0, t1, t2);
-    dst[3 * i] = t0;
-    dst[3 * i + 1] = t1;
-    dst[3 * i + 2] = t2;
+  // four triples per thread per round, their loads and gathers issued together
+  for (uint32_t i0 = tid; i0 < cnt; i0 += 4 * nthreads) {
+    uint32_t t[4][3];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const uint32_t i = i0 + u * nthreads;
+      if (i < cnt) {
+        t[u][0] = slab[3 * i];
+        t[u][1] = slab[3 * i + 1];
+        t[u][2] = slab[3 * i + 2];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (i0 + u * nthreads < cnt) t[u][2] = a.inv[t[u][2]];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const uint32_t i = i0 + u * nthreads;
+      if (i < cnt) {
+        sort3(t[u][0], t[u][1], t[u][2]);
+        dst[3 * i] = t[u][0];
+        dst[3 * i + 1] = t[u][1];
+        dst[3 * i + 2] = t[u][2];
+      }
+    }
   }
 }
 
@@ -262,20 +281,52 @@ __device__ __forceinline__ void scan_items(const ListArgs &a, uint64_t pb, uint6
       const uint64_t Aj = shfl_u64(A, j0) + base;
       const uint32_t iyj = __shfl_sync(0xffffffffu, iy, j0);
       const uint64_t run = (Ej0 < i1 ? Ej0 : i1) - base;
-      for (uint64_t r = 0; r < run; r += 128) {
-        uint32_t z[4];
-        bool act[4];
+      // Each lane takes 4 consecutive elements with one aligned 16-byte load
+      // (out_adj is 256-byte aligned and padded by 4 elements; elements
+      // outside [lo, hi) are masked), and the warp reserves slab room for the
+      // 128 tests of an iteration at once.
+      const uint64_t lo = Aj, hi = Aj + run;
+      for (uint64_t q0 = lo & ~3ull; q0 < hi; q0 += 128) {
+        const uint64_t q = q0 + 4 * lane;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (q < hi) v = *reinterpret_cast<const uint4 *>(a.out_adj + q);
+        const uint32_t z[4] = {v.x, v.y, v.z, v.w};
+        uint32_t hits = 0, nh = 0;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const uint64_t o = r + 32 * u + lane;
-          act[u] = o < run;
-          z[u] = act[u] ? a.out_adj[Aj + o] : 0u;
+          const bool act = q + u >= lo && q + u < hi;
+          probes += act ? 1 : 0;
+          if (act && member(z[u])) {
+            hits |= 1u << u;
+            ++nh;
+          }
         }
+        // warp prefix of hit counts -> slab positions
+        uint32_t incl = nh;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const uint32_t o = __shfl_up_sync(0xffffffffu, incl, d);
+          if (lane >= d) incl += o;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        if (total == 0) continue;
+        uint32_t basepos = 0;
+        if (kWarpSlab) {
+          basepos = wcnt;
+          wcnt += total;
+        } else {
+          if (lane == 31) basepos = atomicAdd(s_cnt, total);
+          basepos = __shfl_sync(0xffffffffu, basepos, 31);
+        }
+        uint32_t r = basepos + incl - nh;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const bool h = act[u] && member(z[u]);
-          probes += act[u] ? 1 : 0;
-          emit(h, iyj, z[u]);
+          if (hits & (1u << u)) {
+            slab[3 * r + 0] = inv_x;
+            slab[3 * r + 1] = iyj;
+            slab[3 * r + 2] = z[u];
+            ++r;
+          }
         }
       }
       base += run;
@@ -350,7 +401,7 @@ __global__ void __launch_bounds__(kWarpThreads, 4) k_list_warp(ListArgs a) {
 //   hash of <= kHashMaxSlots slots, else binary search in the sorted row.
 
 template <int THREADS, int TIER>
-__global__ void __launch_bounds__(THREADS, TIER == 3 ? 1 : 2) k_list_cta(ListArgs a) {
+__global__ void __launch_bounds__(THREADS, TIER == 3 ? 1 : 4) k_list_cta(ListArgs a) {
   extern __shared__ uint32_t sm[];  // bitmap or hash table
   __shared__ int64_t s_t;
   __shared__ uint32_t s_x, s_cnt, s_ok, s_mode, s_lg;
@@ -368,11 +419,9 @@ __global__ void __launch_bounds__(THREADS, TIER == 3 ? 1 : 2) k_list_cta(ListArg
       const int64_t t = fetch_task(a.ctl, a);
       s_t = t;
       if (t >= 0) {
-        // x = the vertex whose piece range contains t
-        const uint64_t nr = a.x_end - a.x_begin;
-        const uint64_t r = upper_bound_u64(a.piece_prefix, nr + 1, (uint64_t)t) - 1;
-        const uint32_t x = a.x_begin + (uint32_t)r;
-        const uint64_t piece = (uint64_t)t - a.piece_prefix[r];
+        // x = the vertex owning task t; the task is its piece t - prefix[x]
+        const uint32_t x = a.task_x[t];
+        const uint64_t piece = (uint64_t)t - a.piece_prefix[x - a.x_begin];
         const uint64_t pb = a.poff[x], pe = a.poff[x + 1];
         const uint64_t p = pe - pb;
         const uint64_t w0 = a.WP[pb], w1 = a.WP[pe];
@@ -387,9 +436,11 @@ __global__ void __launch_bounds__(THREADS, TIER == 3 ? 1 : 2) k_list_cta(ListArg
         if (use_bitmap) {
           s_mode = 0;
         } else {
+          // mid tier: load <= 1/4, so most lookups end at the first slot
           const uint32_t max_slots = TIER == 2 ? (uint32_t)kMidSlots : kHashMaxSlots;
+          const uint64_t want = TIER == 2 ? 4 * p : 2 * p;
           uint32_t lg = 6;
-          while ((1ull << lg) < 2 * p && (1u << lg) < max_slots) ++lg;
+          while ((1ull << lg) < want && (1u << lg) < max_slots) ++lg;
           s_lg = lg;
           s_mode = (2 * p <= (1ull << lg)) ? 1 : 2;  // 2: too large, binary search
         }
@@ -522,6 +573,14 @@ __global__ void k_task_bounds(const uint64_t *__restrict__ wp, uint64_t count, u
   }
 }
 
+__global__ void k_task_owner(const uint64_t *__restrict__ prefix, uint32_t x_begin, uint64_t nr,
+                             uint32_t *__restrict__ task_x) {
+  for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < nr;
+       r += (uint64_t)gridDim.x * blockDim.x) {
+    for (uint64_t t = prefix[r]; t < prefix[r + 1]; ++t) task_x[t] = x_begin + (uint32_t)r;
+  }
+}
+
 // ---- count + hash consumer ---------------------------------------------------
 
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {
@@ -588,6 +647,13 @@ void launch_compact_tier(const uint32_t *flags, const uint64_t *pos, const uint6
 void launch_task_bounds(const uint64_t *wp_list, uint64_t count, uint64_t n_tasks,
                         uint32_t *task_start, cudaStream_t s) {
   k_task_bounds<<<grid_for(n_tasks + 1, 256), 256, 0, s>>>(wp_list, count, n_tasks, task_start);
+  TL_CHECK_LAUNCH();
+}
+
+void launch_task_owner(const uint64_t *piece_prefix, uint32_t x_begin, uint64_t nr,
+                       uint32_t *task_x, cudaStream_t s) {
+  if (nr == 0) return;
+  k_task_owner<<<grid_for(nr, 256), 256, 0, s>>>(piece_prefix, x_begin, nr, task_x);
   TL_CHECK_LAUNCH();
 }
 

@@ -8,7 +8,7 @@ namespace tl {
 // Tiers of B vertices x (by probe-set size p = |P_x| and work W_x):
 //   0 small:  p <= 32,   W <= kWarpWork  -- one warp per x, 64-slot hash per warp
 //   1 medium: p <= 1024, W <= kWarpWork  -- one warp per x, 2048-slot hash per warp
-//   2 mid:    p <= 2048, W >  kWarpWork  -- 256-thread CTA per piece, 4096-slot hash
+//   2 mid:    p <= 2048, W >  kWarpWork  -- 256-thread CTA per piece, 8192-slot hash
 //   3 large:  p >  2048                  -- 1024-thread CTA per piece, bitmap / hash
 constexpr int kTiers = 4;
 constexpr int kWarpThreads = 256;
@@ -16,7 +16,7 @@ constexpr int kMidThreads = 256;
 constexpr int kLargeThreads = 1024;
 constexpr uint32_t kSmallMaxP = 32, kMediumMaxP = 1024, kMidMaxP = 2048;
 constexpr int kSmallSlots = 64, kMediumSlots = 2048;  // per warp, >= 2p (load <= 1/2)
-constexpr int kMidSlots = 4096;                        // per CTA, >= 2p
+constexpr int kMidSlots = 8192;                        // per CTA, >= 4p
 // Work (membership tests) per task: a warp-tier task is owned by one warp
 // and groups vertices up to about kWarpWork units, a vertex weighing its
 // tests plus kVertexCost (its setup is a chain of dependent loads); each
@@ -25,7 +25,7 @@ constexpr int kMidSlots = 4096;                        // per CTA, >= 2p
 // shared by a CTA.
 constexpr uint64_t kWarpWork = 1u << 12;
 constexpr uint64_t kVertexCost = 256;
-constexpr uint64_t kMidPiece = 1u << 15;
+constexpr uint64_t kMidPiece = 1u << 16;
 constexpr uint64_t kPieceWork = 1u << 16;
 constexpr uint64_t kPieceMax = 1u << 18;
 __host__ __device__ inline uint64_t piece_work(int tier, uint64_t p) {
@@ -74,8 +74,10 @@ struct ListArgs {
   const uint64_t *tier_wp;
   const uint32_t *task_start;
   uint64_t tier_count;
-  // mid / large tier: piece prefix over x in [x_begin, x_end) [nr+1]
+  // mid / large tier: piece prefix over x in [x_begin, x_end) [nr+1] and the
+  // vertex of every task [n_tasks]
   const uint64_t *piece_prefix;
+  const uint32_t *task_x;
   int tier;
   ListCtl *ctl;
   uint32_t *chunk;               // output chunk, 3 uint32 per triangle
@@ -104,6 +106,9 @@ void launch_compact_tier(const uint32_t *flags, const uint64_t *pos, const uint6
 // (clamped to count), t in [0, n_tasks].
 void launch_task_bounds(const uint64_t *wp_list, uint64_t count, uint64_t n_tasks,
                         uint32_t *task_start, cudaStream_t s);
+// task_x[t] = the vertex owning task t of a mid or large tier.
+void launch_task_owner(const uint64_t *piece_prefix, uint32_t x_begin, uint64_t nr,
+                       uint32_t *task_x, cudaStream_t s);
 // tier 0, 1: warp kernels; tier 2: mid CTA kernel; tier 3: large CTA kernel.
 void launch_list(int tier, const ListArgs &a, cudaStream_t s);
 int tier_grid(int tier);
