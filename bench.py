@@ -163,7 +163,10 @@ def run_tl(args):
     e_pin = torch.from_numpy(e).pin_memory()
     r_pin = torch.from_numpy(rnk).pin_memory()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    ch = tl.CountHash(stream.cuda_stream)
+    # the consumer reduces each chunk on its own stream, overlapping the
+    # listing kernel that fills the other chunk buffer
+    cstream = torch.cuda.Stream()
+    ch = tl.CountHash(cstream.cuda_stream)
     ch_ptr = tl.tl_count_hash_ptr()
 
     phase_names = ["graph_load", "order_apply", "list_A++", "list_A+-", "graph_free"]

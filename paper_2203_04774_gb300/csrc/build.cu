@@ -103,14 +103,18 @@ __global__ void k_swap_halves(const uint64_t *__restrict__ in, uint64_t m,
 }
 
 // CSR offsets from keys sorted by their high half: off[x] = first index whose
-// high half is >= x, for x in [0, n]; off[n] = m.
+// high half is >= x, for x in [0, n]; off[n] = m.  One binary search per x,
+// so long runs of empty rows cost nothing extra.
 __global__ void k_offsets(const uint64_t *__restrict__ keys, uint64_t m, uint32_t n,
                           uint64_t *__restrict__ off) {
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i <= m;
-       i += (uint64_t)gridDim.x * blockDim.x) {
-    uint64_t cur = (i < m) ? (keys[i] >> 32) : (uint64_t)n;
-    uint64_t prev = (i == 0) ? 0 : (keys[i - 1] >> 32) + 1;
-    for (uint64_t x = prev; x <= cur; ++x) off[x] = i;
+  for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x <= n;
+       x += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t lo = 0, hi = m;
+    while (lo < hi) {
+      const uint64_t mid = (lo + hi) >> 1;
+      if ((keys[mid] >> 32) < x) lo = mid + 1; else hi = mid;
+    }
+    off[x] = lo;
   }
 }
 
@@ -248,14 +252,16 @@ void build_dag(DeviceGraph &g, const uint32_t *rank, bool on_device) {
     radix_sort_u64(ka, kb, m, 0, b, 32, b, g.sort_tmp, g.scan_tmp, s);
     k_low_half<<<grid_for(m, kThreads), kThreads, 0, s>>>(ka, m, g.out_adj.as<uint32_t>());
     TL_CHECK_LAUNCH();
-    k_offsets<<<grid_for(m + 1, kThreads), kThreads, 0, s>>>(ka, m, n, g.out_off.as<uint64_t>());
+    k_offsets<<<grid_for((uint64_t)n + 1, kThreads), kThreads, 0, s>>>(ka, m, n,
+                                                                      g.out_off.as<uint64_t>());
     TL_CHECK_LAUNCH();
     k_swap_halves<<<grid_for(m, kThreads), kThreads, 0, s>>>(ka, m, kb);
     TL_CHECK_LAUNCH();
     radix_sort_u64(kb, ka, m, 0, 0, 32, b, g.sort_tmp, g.scan_tmp, s);
     k_low_half<<<grid_for(m, kThreads), kThreads, 0, s>>>(kb, m, g.in_adj.as<uint32_t>());
     TL_CHECK_LAUNCH();
-    k_offsets<<<grid_for(m + 1, kThreads), kThreads, 0, s>>>(kb, m, n, g.in_off.as<uint64_t>());
+    k_offsets<<<grid_for((uint64_t)n + 1, kThreads), kThreads, 0, s>>>(kb, m, n,
+                                                                      g.in_off.as<uint64_t>());
     TL_CHECK_LAUNCH();
   } else {
     TL_CUDA(cudaMemsetAsync(g.out_off.p, 0, ((uint64_t)n + 1) * 8, s));

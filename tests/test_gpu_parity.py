@@ -236,6 +236,25 @@ def test_count_hash_consumer_matches_oracle():
         assert (nt, cnt, h, probes) == (rc, rc, rh, rp)
 
 
+@pytest.mark.parametrize("offset", [0, 1, 2, 3, 5])
+def test_count_hash_any_alignment_and_length(offset):
+    """The consumer reads 16-byte groups when it can; any start triple and
+    any length gives the oracle's count and hash."""
+    import torch
+    rng = np.random.default_rng(offset)
+    t = np.sort(rng.integers(0, 1 << 31, size=(100_003, 3), dtype=np.uint32), axis=1)
+    dev = torch.from_numpy(t.view(np.int32)).cuda()
+    for n in (0, 1, 7, 4096, len(t) - offset):
+        sub = t[offset:offset + n]
+        ch = tl.CountHash()
+        try:
+            rc = tl.lib().tl_count_hash(dev.data_ptr() + 12 * offset, n, 0, ch.user)
+            assert rc == 0
+            assert (int(ch.state.count), int(ch.state.hash)) == (n, oracle.hash_triples(sub))
+        finally:
+            ch.release()
+
+
 def test_every_tier_runs_and_matches():
     """Chung-Lu graph plus a wheel (hub joined to a 5000-cycle): probe sets of
     every size, so all four listing kernels (small, medium, mid, large with
