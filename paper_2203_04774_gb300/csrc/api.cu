@@ -103,6 +103,14 @@ struct tl_graph {
 
 namespace {
 
+// Build the DAG of the identity ordering if no ordering has been applied yet.
+void ensure_ordered(tl_graph *G) {
+  if (!G->g.ordered) {
+    G->cached_alg = -1;
+    tl::build_dag(G->g, nullptr, true);
+  }
+}
+
 void require_device() {
   int count = 0;
   cudaError_t e = cudaGetDeviceCount(&count);
@@ -195,7 +203,7 @@ tl_status list_impl(tl_graph *G, int alg, uint32_t xb, uint32_t xe, size_t chunk
   if (!G) tl::fail(TL_EINVAL, "graph is NULL");
   if (alg != TL_APP && alg != TL_APM) tl::fail(TL_EINVAL, "alg must be TL_APP or TL_APM");
   tl::DeviceGraph &g = G->g;
-  if (!g.ordered) tl::fail(TL_ESTATE, "no ordering applied");
+  ensure_ordered(G);
   if (xb > xe || xe > g.n) tl::fail(TL_EINVAL, "seed range outside [0, n]");
   if (chunk_bytes < TL_MIN_CHUNK_BYTES) tl::fail(TL_EINVAL, "chunk_bytes below TL_MIN_CHUNK_BYTES");
   const uint64_t cap = chunk_bytes / 12;
@@ -359,20 +367,8 @@ tl_status tl_graph_load(tl_graph **out, uint32_t n, const uint32_t *edges, uint6
     G->g.n = n;
     G->bind(static_cast<cudaStream_t>(stream));
     tl::build_edge_set(G->g, edges, m_in, edges_on_device != 0);
-    // identity ordering (the dataset's original ordering)
-    tl::DevBuf ident(G->g.stream);
-    ident.reserve((uint64_t)n * 4);
-    {
-      uint32_t *h = nullptr;
-      TL_CUDA(cudaMallocHost(&h, (uint64_t)n * 4));
-      for (uint32_t v = 0; v < n; ++v) h[v] = v;
-      cudaError_t e = cudaMemcpyAsync(ident.p, h, (uint64_t)n * 4, cudaMemcpyHostToDevice,
-                                      G->g.stream);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(G->g.stream);
-      cudaFreeHost(h);
-      TL_CUDA(e);
-    }
-    tl::build_dag(G->g, ident.as<uint32_t>(), true);
+    // The identity ordering (the dataset's original one) is built lazily, on
+    // the first call that needs a DAG before any tl_order_apply.
   } catch (...) {
     delete G;
     throw;
@@ -401,7 +397,7 @@ tl_status tl_cost(const tl_graph *G, tl_alg alg, uint64_t *cost) {
   TL_API_BEGIN
   if (!G || !cost) tl::fail(TL_EINVAL, "graph or cost is NULL");
   if (alg != TL_APP && alg != TL_APM) tl::fail(TL_EINVAL, "alg must be TL_APP or TL_APM");
-  if (!G->g.ordered) tl::fail(TL_ESTATE, "no ordering applied");
+  ensure_ordered(const_cast<tl_graph *>(G));
   *cost = (alg == TL_APP) ? G->g.cost_app : G->g.cost_apm;
   TL_API_END
 }
@@ -454,7 +450,7 @@ tl_status tl_graph_csr(const tl_graph *G, int dir, uint64_t *off, uint32_t *adj)
   TL_API_BEGIN
   if (!G || !off || !adj) tl::fail(TL_EINVAL, "NULL argument");
   if (dir != 0 && dir != 1) tl::fail(TL_EINVAL, "dir must be 0 (N+) or 1 (N-)");
-  if (!G->g.ordered) tl::fail(TL_ESTATE, "no ordering applied");
+  ensure_ordered(const_cast<tl_graph *>(G));
   const tl::DeviceGraph &g = G->g;
   const tl::DevBuf &o = dir == 0 ? g.out_off : g.in_off;
   const tl::DevBuf &d = dir == 0 ? g.out_adj : g.in_adj;

@@ -67,6 +67,12 @@ __global__ void k_rank_check(const uint32_t *__restrict__ cnt, uint32_t n,
   }
 }
 
+__global__ void k_iota(uint32_t *__restrict__ v, uint32_t n) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    v[i] = (uint32_t)i;
+}
+
 __global__ void k_inverse(const uint32_t *__restrict__ rank, uint32_t n,
                           uint32_t *__restrict__ inv) {
   for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
@@ -214,8 +220,13 @@ void build_dag(DeviceGraph &g, const uint32_t *rank, bool on_device) {
   // a2: the ordering must be a permutation of [0, n).
   DevBuf rank_new(s), cnt(s);
   rank_new.reserve((uint64_t)n * 4);
-  TL_CUDA(cudaMemcpyAsync(rank_new.p, rank, (uint64_t)n * 4,
-                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  if (rank) {
+    TL_CUDA(cudaMemcpyAsync(rank_new.p, rank, (uint64_t)n * 4,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  } else {  // the identity ordering
+    k_iota<<<grid_for(n, kThreads), kThreads, 0, s>>>(rank_new.as<uint32_t>(), n);
+    TL_CHECK_LAUNCH();
+  }
   cnt.reserve((uint64_t)n * 4);
   TL_CUDA(cudaMemsetAsync(cnt.p, 0, (uint64_t)n * 4, s));
   k_rank_hist<<<grid_for(n, kThreads), kThreads, 0, s>>>(rank_new.as<uint32_t>(), n,

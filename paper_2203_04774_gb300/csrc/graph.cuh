@@ -32,6 +32,7 @@ struct DeviceGraph {
 // a1: copy + canonicalise + dedup (build.cu).  Throws tl::Error.
 void build_edge_set(DeviceGraph &g, const uint32_t *edges, uint64_t m_in, bool on_device);
 // a2-a5: validate the permutation, relabel, orient, CSR out/in, cost.
+// rank == nullptr applies the identity ordering.
 void build_dag(DeviceGraph &g, const uint32_t *rank, bool on_device);
 
 }  // namespace tl

@@ -138,9 +138,11 @@ __device__ __forceinline__ void copy_out(const ListArgs &a, const uint32_t *slab
       const uint32_t i = i0 + u * nthreads;
       if (i < cnt) {
         sort3(t[u][0], t[u][1], t[u][2]);
-        dst[3 * i] = t[u][0];
-        dst[3 * i + 1] = t[u][1];
-        dst[3 * i + 2] = t[u][2];
+        // streaming stores: the chunk is read once by the consumer, so it
+        // should not evict the adjacency lists from L2
+        __stcs(dst + 3 * i, t[u][0]);
+        __stcs(dst + 3 * i + 1, t[u][1]);
+        __stcs(dst + 3 * i + 2, t[u][2]);
       }
     }
   }
@@ -607,7 +609,7 @@ __global__ void k_count_hash(const uint32_t *__restrict__ t, uint64_t n,
   const uint64_t groups = aligned ? n / 4 : 0;
   const uint4 *t4 = reinterpret_cast<const uint4 *>(t);
   for (uint64_t gi = tid; gi < groups; gi += stride) {
-    const uint4 p = t4[3 * gi], q = t4[3 * gi + 1], r = t4[3 * gi + 2];
+    const uint4 p = __ldcs(t4 + 3 * gi), q = __ldcs(t4 + 3 * gi + 1), r = __ldcs(t4 + 3 * gi + 2);
     h += triple_hash(p.x, p.y, p.z) + triple_hash(p.w, q.x, q.y) + triple_hash(q.z, q.w, r.x) +
          triple_hash(r.y, r.z, r.w);
   }
