@@ -90,6 +90,20 @@ TL_EXPORT tl_status tl_graph_size(const tl_graph *g, uint32_t *n, uint64_t *m);
  * TL_EINVAL, and the previous ordering stays in force. */
 TL_EXPORT tl_status tl_order_apply(tl_graph *g, const uint32_t *rank, int rank_on_device);
 
+/* Orderings computed on the device from the loaded graph's degrees d_v
+ * (Sec. 1.3), written as ranks (rank[v] = pi_v - 1) to `rank` (n uint32;
+ * host pointer if rank_on_device == 0, else device pointer; caller-owned):
+ *   TL_ORDER_DEGREE: non-decreasing degree, ties by increasing id -- the
+ *                    degree ordering of Sec. 2.2;
+ *   TL_ORDER_SPLIT:  the Split heuristic of Sec. 3.3.3 -- vertices by
+ *                    non-increasing degree (ties by increasing id), the one at
+ *                    1-based position 2i+1 gets pi = i+1, the one at 2i gets
+ *                    pi = n+1-i.
+ * The ordering is not applied; pass it to tl_order_apply. */
+typedef enum { TL_ORDER_DEGREE = 0, TL_ORDER_SPLIT = 1 } tl_order_kind;
+TL_EXPORT tl_status tl_order_compute(tl_graph *g, tl_order_kind kind, uint32_t *rank,
+                                     int rank_on_device);
+
 /* Cost of the current ordering (Sec. 3.1): TL_APP -> C++ = sum_u d+_u^2,
  * TL_APM -> C+- = sum_u d+_u d-_u.  Exact, uint64.  By Property 1 this is
  * the number of neighbour tests the chosen algorithm performs. */

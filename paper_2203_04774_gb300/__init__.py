@@ -52,6 +52,7 @@ SIGNATURES = {
     "tl_graph_load": ([ctypes.POINTER(_P), _U32, _P, _U64, _I, _P], _I),
     "tl_graph_size": ([_P, ctypes.POINTER(_U32), ctypes.POINTER(_U64)], _I),
     "tl_order_apply": ([_P, _P, _I], _I),
+    "tl_order_compute": ([_P, _I, _P, _I], _I),
     "tl_cost": ([_P, _I, ctypes.POINTER(_U64)], _I),
     "tl_list_triangles": ([_P, _I, _SZ, _P, _P, ctypes.POINTER(_U64)], _I),
     "tl_list_triangles_range": ([_P, _I, _U32, _U32, _SZ, _P, _P, ctypes.POINTER(_U64),
@@ -143,6 +144,21 @@ def tl_graph_size(g) -> tuple[int, int]:
 def tl_order_apply(g, rank) -> None:
     ptr, on_dev, keep = _ptr_and_flag(rank)
     _check(lib().tl_order_apply(g, ptr, on_dev), "tl_order_apply")
+
+
+TL_ORDER_DEGREE, TL_ORDER_SPLIT = 0, 1
+
+
+def tl_order_compute(g, kind: int, rank=None):
+    """Degree or Split ordering computed on the device.  With ``rank`` None a
+    host uint32 array is returned; else ``rank`` (numpy or torch, n uint32)
+    is filled in place."""
+    if rank is None:
+        n, _ = tl_graph_size(g)
+        rank = np.empty(n, dtype=np.uint32)
+    ptr, on_dev, keep = _ptr_and_flag(rank)
+    _check(lib().tl_order_compute(g, kind, ptr, on_dev), "tl_order_compute")
+    return rank
 
 
 def tl_cost(g, alg: int) -> int:

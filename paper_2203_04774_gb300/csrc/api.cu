@@ -28,7 +28,7 @@ cudaMemPool_t device_pool() {
   if (!pools[dev]) {
     cudaMemPool_t p;
     TL_CUDA(cudaDeviceGetDefaultMemPool(&p, dev));
-    uint64_t keep = ~0ull;
+    uint64_t keep = 8ull << 30;  // cached for reuse; the rest goes back at sync points
     TL_CUDA(cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep));
     pools[dev] = p;
   }
@@ -390,6 +390,15 @@ tl_status tl_order_apply(tl_graph *G, const uint32_t *rank, int rank_on_device) 
   if (!G || !rank) tl::fail(TL_EINVAL, "graph or rank is NULL");
   G->cached_alg = -1;
   tl::build_dag(G->g, rank, rank_on_device != 0);
+  TL_API_END
+}
+
+tl_status tl_order_compute(tl_graph *G, tl_order_kind kind, uint32_t *rank, int rank_on_device) {
+  TL_API_BEGIN
+  if (!G || !rank) tl::fail(TL_EINVAL, "graph or rank is NULL");
+  if (kind != TL_ORDER_DEGREE && kind != TL_ORDER_SPLIT)
+    tl::fail(TL_EINVAL, "kind must be TL_ORDER_DEGREE or TL_ORDER_SPLIT");
+  tl::compute_order(G->g, kind, rank, rank_on_device != 0);
   TL_API_END
 }
 

@@ -155,6 +155,43 @@ __global__ void k_cost(const uint64_t *__restrict__ out_off, const uint64_t *__r
   }
 }
 
+// d_v of every vertex from the cleaned edge set (each key counts for both ends).
+__global__ void k_degrees(const uint64_t *__restrict__ E, uint64_t m, uint32_t *__restrict__ deg) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t e = E[i];
+    atomicAdd(&deg[(uint32_t)(e >> 32)], 1u);
+    atomicAdd(&deg[(uint32_t)e], 1u);
+  }
+}
+
+// key[v] = sort value << 32 | v, the sort value being d_v (ascending degree)
+// or (2^bits - 1 - d_v) (descending degree); keys start in id order, so a
+// stable sort on the high half breaks ties by increasing id.
+__global__ void k_degree_keys(const uint32_t *__restrict__ deg, uint32_t n, int descending,
+                              uint32_t top, uint64_t *__restrict__ keys) {
+  for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
+       v += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t d = descending ? top - deg[v] : deg[v];
+    keys[v] = (uint64_t)d << 32 | v;
+  }
+}
+
+// Ranks from the sorted sequence: position p of vertex v gives rank p
+// (degree ordering), or the Split rule of Sec. 3.3.3 on the 1-based position
+// p+1 of the non-increasing degree sequence: p+1 = 2i+1 -> pi = i+1,
+// p+1 = 2i -> pi = n+1-i (0-based rank = pi - 1).
+__global__ void k_ranks_from_sequence(const uint64_t *__restrict__ keys, uint32_t n, int split,
+                                      uint32_t *__restrict__ rank) {
+  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < n;
+       p += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t v = (uint32_t)keys[p];
+    uint64_t r = p;
+    if (split) r = (p % 2 == 0) ? p / 2 : (uint64_t)n - (p + 1) / 2;
+    rank[v] = (uint32_t)r;
+  }
+}
+
 template <class T>
 T read_scalar(const T *dev, cudaStream_t s) {
   T v;
@@ -290,6 +327,43 @@ void build_dag(DeviceGraph &g, const uint32_t *rank, bool on_device) {
   g.max_out_deg = (uint32_t)h[2];
   g.max_in_deg = (uint32_t)h[3];
   g.ordered = true;
+}
+
+}  // namespace tl
+
+namespace tl {
+
+void compute_order(DeviceGraph &g, int kind, uint32_t *rank, bool on_device) {
+  cudaStream_t s = g.stream;
+  const uint32_t n = g.n;
+  DevBuf deg(s), ka(s), kb(s), out(s), tmp(s), scan(s);
+  deg.reserve((uint64_t)n * 4);
+  ka.reserve((uint64_t)n * 8);
+  kb.reserve((uint64_t)n * 8);
+  TL_CUDA(cudaMemsetAsync(deg.p, 0, (uint64_t)n * 4, s));
+  if (g.m) {
+    k_degrees<<<grid_for(g.m, kThreads), kThreads, 0, s>>>(g.E.as<uint64_t>(), g.m,
+                                                           deg.as<uint32_t>());
+    TL_CHECK_LAUNCH();
+  }
+  const int bits = bits_for(n);  // degrees are < n < 2^bits
+  const uint32_t top = (uint32_t)((1ull << bits) - 1);
+  const int split = kind == TL_ORDER_SPLIT;
+  k_degree_keys<<<grid_for(n, kThreads), kThreads, 0, s>>>(deg.as<uint32_t>(), n, split, top,
+                                                           ka.as<uint64_t>());
+  TL_CHECK_LAUNCH();
+  radix_sort_u64(ka.as<uint64_t>(), kb.as<uint64_t>(), n, 0, 0, 32, bits, tmp, scan, s);
+  uint32_t *dst = rank;
+  if (!on_device) {
+    out.reserve((uint64_t)n * 4);
+    dst = out.as<uint32_t>();
+  }
+  k_ranks_from_sequence<<<grid_for(n, kThreads), kThreads, 0, s>>>(ka.as<uint64_t>(), n, split,
+                                                                   dst);
+  TL_CHECK_LAUNCH();
+  if (!on_device)
+    TL_CUDA(cudaMemcpyAsync(rank, dst, (uint64_t)n * 4, cudaMemcpyDeviceToHost, s));
+  TL_CUDA(cudaStreamSynchronize(s));
 }
 
 }  // namespace tl

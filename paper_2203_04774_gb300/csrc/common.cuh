@@ -44,8 +44,8 @@ inline void fail(tl_status s, const std::string &msg) { throw Error{s, msg}; }
 
 // ---- device buffer (RAII, stream-ordered) ------------------------------------
 
-// The current device's default memory pool, set once per device to keep
-// freed memory cached (release threshold = unlimited) so that buffers of
+// The current device's default memory pool, set once per device to keep up
+// to 8 GiB of freed memory cached (release threshold) so that buffers of
 // repeated calls are recycled without driver round trips.
 cudaMemPool_t device_pool();
 

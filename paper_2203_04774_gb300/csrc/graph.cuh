@@ -34,5 +34,7 @@ void build_edge_set(DeviceGraph &g, const uint32_t *edges, uint64_t m_in, bool o
 // a2-a5: validate the permutation, relabel, orient, CSR out/in, cost.
 // rank == nullptr applies the identity ordering.
 void build_dag(DeviceGraph &g, const uint32_t *rank, bool on_device);
+// Degree (kind 0) or Split (kind 1) ordering of the loaded graph into rank[n].
+void compute_order(DeviceGraph &g, int kind, uint32_t *rank, bool on_device);
 
 }  // namespace tl

@@ -306,3 +306,33 @@ def test_large_n_hash_probe_path():
             nt, cnt, h, probes = g.list_count_hash(alg)
             _, rc, rh, rp = ref.list(alg, store=False)
             assert (nt, h, probes) == (rc, rh, rp), (name, alg)
+
+
+@pytest.mark.parametrize("kind", ["degree", "split"])
+def test_device_orderings_match_host(kind):
+    """tl_order_compute (degree ordering of Sec. 2.2, Split of Sec. 3.3.3) is
+    bit-identical to the host orderings, ties by id included."""
+    import torch
+    for n, e in [(7, synth.fig3_graph()), (3000, synth.chung_lu(3000, 12, 2.3, 8)),
+                 (5000, synth.complete_bipartite(10, 4990)), (4000, synth.star(4000, 11)),
+                 (1, np.zeros((0, 2), np.uint32))]:
+        off, _ = synth.simple_csr(n, e)
+        want = synth.order_degree(off) if kind == "degree" else synth.order_split(off)
+        g = tl.Graph(n, _dev(e))
+        k = tl.TL_ORDER_DEGREE if kind == "degree" else tl.TL_ORDER_SPLIT
+        assert np.array_equal(tl.tl_order_compute(g.h, k), want), (n, kind)
+        dev_rank = torch.empty(n, dtype=torch.int32, device="cuda")
+        tl.tl_order_compute(g.h, k, dev_rank)
+        assert np.array_equal(dev_rank.cpu().numpy().view(np.uint32), want)
+        g.order_apply(dev_rank)  # usable directly as an ordering
+        ref = oracle.Graph(n, e)
+        ref.order_apply(want)
+        assert g.cost(tl.TL_APP) == ref.cost(tl.TL_APP)
+        g.free()
+
+
+def test_device_generator_on_gpu_matches_host():
+    from paper_2203_04774_gb300.synth import device as dev
+    e = synth.chung_lu(50000, 20, 2.2, 4)
+    t = dev.chung_lu_device(50000, 20, 2.2, 4, device="cuda", block=1 << 16)
+    assert np.array_equal(e, t.cpu().numpy().view(np.uint32))

@@ -96,3 +96,16 @@ def test_neigh_and_check_lower_cpm():
     c_check = g.cost(oracle.APM)
     g.order_apply(synth.order_random(n, 1))
     assert c_check < g.cost(oracle.APM)
+
+
+def test_device_generator_matches_host_generator():
+    """The torch (device) Chung-Lu generator draws exactly the host edges;
+    checked here with torch on the CPU."""
+    torch = pytest.importorskip("torch")
+    from paper_2203_04774_gb300.synth import device as dev
+    e = synth.chung_lu(20000, 16, 2.2, 7)
+    t = dev.chung_lu_device(20000, 16, 2.2, 7, device="cpu", block=30000)
+    assert t.dtype == torch.int32
+    assert np.array_equal(e, t.numpy().view(np.uint32))
+    assert np.array_equal(synth.counter_uniform(3, 1, 1000, start=77),
+                          dev.counter_uniform_t(3, 1, 1000, 77, "cpu").numpy())
