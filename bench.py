@@ -57,6 +57,28 @@ def gen_inputs():
     return n, e, rank
 
 
+def gen_inputs_device(torch, tl):
+    from paper_2203_04774_gb300.synth import device as dev
+    n = WORKLOAD["n"]
+    e = dev.chung_lu_device(n, WORKLOAD["avg_degree"], WORKLOAD["exponent"], WORKLOAD["seed"])
+    g = tl.tl_graph_load(n, e)
+    try:
+        rank = torch.empty(n, dtype=torch.int32, device="cuda")
+        tl.tl_order_compute(g, tl.TL_ORDER_DEGREE, rank)
+    finally:
+        tl.tl_graph_free(g)
+    return n, e, rank
+
+
+WORKLOADS = {
+    "rmat20": WORKLOAD,
+    "chunglu1e8": {"workload": "chunglu1e8-degree", "generator": "Chung-Lu", "n": 100_000_000,
+                   "avg_degree": 40, "exponent": 2.2, "seed": 4,
+                   "ordering": "degree (ties by id), computed on the device",
+                   "algorithms": ["A++", "A+-"]},
+}
+
+
 def read_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -155,13 +177,22 @@ def run_tl(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     t0 = time.time()
-    n, e, rnk = gen_inputs()
-    log(f"[bench] inputs ready in {time.time() - t0:.1f}s: n={n} pairs={len(e)}")
+    if WORKLOAD["generator"] == "Chung-Lu":
+        # too large for the host: edges drawn on the device, degree ordering
+        # computed on the device (both before the timed region)
+        n, e_dev, r_dev = gen_inputs_device(torch, tl)
+        e = rnk = None
+        args.no_cpu = args.no_orderings = args.no_e2e = True
+        npairs = e_dev.shape[0]
+    else:
+        n, e, rnk = gen_inputs()
+        e_dev = torch.from_numpy(e).cuda()
+        r_dev = torch.from_numpy(rnk).cuda()
+        npairs = len(e)
+    log(f"[bench] inputs ready in {time.time() - t0:.1f}s: n={n} pairs={npairs}")
     stream = torch.cuda.Stream()
-    e_dev = torch.from_numpy(e).cuda()
-    r_dev = torch.from_numpy(rnk).cuda()
-    e_pin = torch.from_numpy(e).pin_memory()
-    r_pin = torch.from_numpy(rnk).pin_memory()
+    e_pin = torch.from_numpy(e).pin_memory() if e is not None else None
+    r_pin = torch.from_numpy(rnk).pin_memory() if rnk is not None else None
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     # the consumer reduces each chunk on its own stream, overlapping the
     # listing kernel that fills the other chunk buffer
@@ -273,7 +304,7 @@ def run_tl(args):
                            parallelism="replicas" if world > 1 else "1 GPU"),
             "oriented_edges_per_s": m * 2 * args.steps * world / (total_ms / 1e3),
             "e2e": {"value": e2e_value, "unit": "triangles/s",
-                    "h2d_bytes_per_step": int(e.nbytes + rnk.nbytes),
+                    "h2d_bytes_per_step": int(e.nbytes + rnk.nbytes) if e is not None else None,
                     "d2h_bytes_per_step": 2 * 16},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
@@ -399,12 +430,19 @@ def main():
                     help="R-MAT scale (20 is the measured workload; smaller for profiling)")
     ap.add_argument("--chunk-mb", type=int, default=DEFAULT_CHUNK_MB,
                     help="output chunk size in MiB")
+    ap.add_argument("--workload", default="rmat20", choices=sorted(WORKLOADS),
+                    help="rmat20: the measured workload; chunglu1e8: the 2e9-edge graph")
     args = ap.parse_args()
-    global CHUNK_BYTES
+    global CHUNK_BYTES, WORKLOAD
     CHUNK_BYTES = args.chunk_mb << 20
-    if args.scale != 20:
+    WORKLOAD = WORKLOADS[args.workload]
+    if args.scale != 20 and args.workload == "rmat20":
         WORKLOAD["scale"] = args.scale
         WORKLOAD["workload"] = f"rmat{args.scale}-degree"
+    if args.impl == "reference" and args.workload != "rmat20":
+        print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle cannot hold the "
+                          "2e9-edge graph; its reference arm runs on rmat20 only"}))
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -55,7 +55,7 @@ struct PinnedCtl {
 struct tl_graph {
   tl::DeviceGraph g;
   // listing workspace
-  tl::DevBuf wseed, WP, ctl, chunks, slabs, retry;
+  tl::DevBuf wseed, WP, ctl, chunks, slabs, retry, ghash;
   // per-vertex classification (tiers 0, 1: weights and flags; tiers 2, 3: pieces),
   // their prefixes, and the compacted vertex lists of tiers 0 and 1
   tl::DevBuf tw[2], tf[2], tpref[2], tpos[2], tx[2], twp[2], tstart[2], pieces[2],
@@ -69,7 +69,7 @@ struct tl_graph {
   uint64_t tier_count[2] = {0, 0};
   void bind(cudaStream_t s) {
     g.bind(s);
-    for (tl::DevBuf *b : {&wseed, &WP, &ctl, &chunks, &slabs, &retry}) b->stream = s;
+    for (tl::DevBuf *b : {&wseed, &WP, &ctl, &chunks, &slabs, &retry, &ghash}) b->stream = s;
     for (int t = 0; t < 2; ++t)
       for (tl::DevBuf *b : {&tw[t], &tf[t], &tpref[t], &tpos[t], &tx[t], &twp[t], &tstart[t],
                             &pieces[t], &piece_prefix[t], &task_x[t]})
@@ -221,6 +221,10 @@ tl_status list_impl(tl_graph *G, int alg, uint32_t xb, uint32_t xe, size_t chunk
   }
   G->chunks.reserve(2 * cap * 12);
   G->slabs.reserve(slab_words * 12);
+  // hub tables in global memory, needed only when the bitmap over all ranks
+  // does not fit in shared memory
+  const bool need_ghash = g.n > tl::kBitmapMaxN && G->n_tasks[3] > 0;
+  if (need_ghash) G->ghash.reserve((uint64_t)tl::tier_grid(3) * tl::kGHashSlots * 4);
   G->retry.reserve(2 * max_tasks * 4);
   G->ctl.reserve(sizeof(tl::ListCtl));
   if (!G->pctl) G->pctl = new tl::PinnedCtl();
@@ -241,6 +245,7 @@ tl_status list_impl(tl_graph *G, int alg, uint32_t xb, uint32_t xe, size_t chunk
   a.ctl = G->ctl.as<tl::ListCtl>();
   a.chunk_cap = cap;
   a.slabs = G->slabs.as<uint32_t>();
+  a.ghash = need_ghash ? G->ghash.as<uint32_t>() : nullptr;
 
   if (!G->ev[0]) {
     TL_CUDA(cudaEventCreate(&G->ev[0]));

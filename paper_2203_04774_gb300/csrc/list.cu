@@ -103,6 +103,22 @@ __device__ __forceinline__ bool hash_find(const uint32_t *H, int lg, uint32_t z)
   }
 }
 
+// Filter bit of rank r (2^20 bits) for the hub tier's shared-memory filter.
+__device__ __forceinline__ uint32_t fslot(uint32_t r) { return (r * 0x85EBCA77u) >> 12; }
+
+// Lookup in a hash table in global memory that this CTA filled with atomics
+// at the L2: read past the L1, which may hold lines of an earlier task's table.
+__device__ __forceinline__ bool hash_find_global(const uint32_t *H, int lg, uint32_t z) {
+  const uint32_t mask = (1u << lg) - 1u;
+  uint32_t h = hslot(z, lg);
+  for (;;) {
+    const uint32_t v = __ldcg(H + h);
+    if (v == z) return true;
+    if (v == kEmpty) return false;
+    h = (h + 1) & mask;
+  }
+}
+
 // Task fetch shared by all kernels: returns the task id or -1.  Thread 0
 // only; the caller broadcasts.
 __device__ __forceinline__ int64_t fetch_task(ListCtl *ctl, const ListArgs &a) {
@@ -398,9 +414,11 @@ __global__ void __launch_bounds__(kWarpThreads, 4) k_list_warp(ListArgs a) {
 }
 
 // ---- mid and large vertices: one CTA per piece, B shared by the CTA -------
-//   TIER 2 (mid, p <= 2048): open-addressing hash of <= 4096 slots.
-//   TIER 3 (large): a bitmap over all ranks when n <= kBitmapMaxN, else a
-//   hash of <= kHashMaxSlots slots, else binary search in the sorted row.
+//   TIER 2 (mid, p <= 2048): open-addressing hash of <= 8192 slots.
+//   TIER 3 (large): a bitmap over all ranks when n <= kBitmapMaxN (mode 0),
+//   else a hash of <= kHashMaxSlots slots (mode 1), else a filter in shared
+//   memory + the CTA's hash table in global memory (mode 3), else binary
+//   search in the sorted row (mode 2).
 
 template <int THREADS, int TIER>
 __global__ void __launch_bounds__(THREADS, TIER == 3 ? 1 : 4) k_list_cta(ListArgs a) {
@@ -445,6 +463,13 @@ __global__ void __launch_bounds__(THREADS, TIER == 3 ? 1 : 4) k_list_cta(ListArg
           while ((1ull << lg) < want && (1u << lg) < max_slots) ++lg;
           s_lg = lg;
           s_mode = (2 * p <= (1ull << lg)) ? 1 : 2;  // 2: too large, binary search
+          if (TIER == 3 && s_mode == 2 && a.ghash && 2 * p <= kGHashSlots) {
+            // 3: shared-memory filter + this CTA's hash table in global memory
+            lg = 6;
+            while ((1ull << lg) < 2 * p) ++lg;
+            s_lg = lg;
+            s_mode = 3;
+          }
         }
       }
     }
@@ -465,6 +490,17 @@ __global__ void __launch_bounds__(THREADS, TIER == 3 ? 1 : 4) k_list_cta(ListArg
       for (uint32_t i = threadIdx.x; i < (1u << lg); i += THREADS) sm[i] = kEmpty;
       __syncthreads();
       for (uint64_t q = pb + threadIdx.x; q < pe; q += THREADS) hash_insert(sm, lg, a.padj[q]);
+    } else if (mode == 3) {
+      uint32_t *gh = a.ghash + (uint64_t)blockIdx.x * kGHashSlots;
+      for (uint32_t i = threadIdx.x; i < kFilterWords; i += THREADS) sm[i] = 0;
+      for (uint32_t i = threadIdx.x; i < (1u << lg); i += THREADS) gh[i] = kEmpty;
+      __syncthreads();
+      for (uint64_t q = pb + threadIdx.x; q < pe; q += THREADS) {
+        const uint32_t r = a.padj[q];
+        const uint32_t f = fslot(r);
+        atomicOr(&sm[f >> 5], 1u << (f & 31));
+        hash_insert(gh, lg, r);
+      }
     }
     __syncthreads();
     // the piece's tests, split into one contiguous range per warp
@@ -485,6 +521,15 @@ __global__ void __launch_bounds__(THREADS, TIER == 3 ? 1 : 4) k_list_cta(ListArg
       scan_items<false>(a, pb, pe, ~0ull, wa, wb, inv_x,
                         [&](uint32_t z) { return hash_find(sm, lg, z); }, slab, &s_cnt, unused,
                         probes);
+    } else if (mode == 3) {
+      const uint32_t *gh = a.ghash + (uint64_t)blockIdx.x * kGHashSlots;
+      scan_items<false>(a, pb, pe, ~0ull, wa, wb, inv_x,
+                        [&](uint32_t z) {
+                          const uint32_t f = fslot(z);
+                          if (((sm[f >> 5] >> (f & 31)) & 1u) == 0) return false;
+                          return hash_find_global(gh, lg, z);
+                        },
+                        slab, &s_cnt, unused, probes);
     } else {
       scan_items<false>(a, pb, pe, ~0ull, wa, wb, inv_x,
                         [&](uint32_t z) {

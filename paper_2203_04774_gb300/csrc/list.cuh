@@ -37,6 +37,11 @@ __host__ __device__ inline uint64_t piece_work(int tier, uint64_t p) {
 // Shared-memory probe structures of the large kernel.
 constexpr uint32_t kBitmapMaxN = 1572864u;               // 192 KiB bitmap over ranks
 constexpr uint32_t kHashMaxSlots = 32768u;               // 128 KiB hash table
+// Hubs too large for the shared-memory table when n > kBitmapMaxN: a 2^20-bit
+// shared-memory filter over hashed ranks in front of a per-CTA hash table of
+// kGHashSlots slots in global memory (p <= kGHashSlots / 2).
+constexpr uint32_t kFilterWords = 1u << 15;
+constexpr uint32_t kGHashSlots = 1u << 18;
 constexpr int kLargeSmemBytes = (int)(kBitmapMaxN / 8);  // >= kHashMaxSlots * 4
 // Triangles a task can produce (bounded by its work): per warp for the warp
 // tiers, per CTA for the mid and large tiers.
@@ -78,6 +83,7 @@ struct ListArgs {
   // vertex of every task [n_tasks]
   const uint64_t *piece_prefix;
   const uint32_t *task_x;
+  uint32_t *ghash;               // large tier, n > kBitmapMaxN: kGHashSlots per CTA (or null)
   int tier;
   ListCtl *ctl;
   uint32_t *chunk;               // output chunk, 3 uint32 per triangle

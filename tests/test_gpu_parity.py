@@ -293,7 +293,12 @@ def test_large_n_hash_probe_path():
     e1 = synth.chung_lu(n, 4, 2.1, 12)
     hub = np.stack([np.zeros(40000, np.uint32), np.arange(1, 40001, dtype=np.uint32)], 1)
     ring = np.stack([np.arange(1, 40000, dtype=np.uint32), np.arange(2, 40001, dtype=np.uint32)], 1)
-    e = np.concatenate([e1, hub, ring])
+    # a second hub with 150,000 neighbours: beyond the global hash table too
+    h2 = 1_000_000
+    leaves = np.arange(h2 + 1, h2 + 150_001, dtype=np.uint32)
+    hub2 = np.stack([np.full_like(leaves, h2), leaves], 1)
+    ring2 = np.stack([leaves[:-1], leaves[1:]], 1)
+    e = np.concatenate([e1, hub, ring, hub2, ring2])
     off, _ = synth.simple_csr(n, e)
     orders = [("degree", synth.order_degree(off)), ("identity", synth.order_identity(n)),
               ("reverse", (n - 1 - np.arange(n)).astype(np.uint32))]
