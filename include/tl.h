@@ -80,6 +80,42 @@ typedef enum {
 TL_EXPORT tl_status tl_graph_load(tl_graph **out, uint32_t n, const uint32_t *edges,
                         uint64_t m_in, int edges_on_device, void *stream);
 
+/* Disjoint unions: many independent graphs as one graph, so that one build
+ * and one listing pass serve all of them.  The paper has no counterpart (it
+ * lists one graph at a time); what makes it exact is that no edge joins two
+ * parts, so each triangle of the union (three pairwise adjacent vertices,
+ * Sec. 1.3) lies inside one part and the union's triangles are the parts'.
+ * Layout: part i's vertex v is the union's vertex vbase_i + v, where
+ * vbase_i = n_0 + ... + n_{i-1}; the union has n = n_0 + ... + n_{k-1}
+ * vertices (< 2^32 - 1, else TL_EINVAL).  The union's triples carry union
+ * ids; tl_count_hash_parts maps them back to (part, local ids).
+ *
+ * tl_graph_load_parts: k >= 1 graphs given as one concatenated edge list.
+ *   n      host array of k part sizes, each >= 1.
+ *   m_in   host array of k pair counts; part i's pairs follow part i-1's.
+ *   edges  2 * sum(m_in) uint32 part-local ids (host or device pointer as in
+ *          tl_graph_load); an id >= its part's n -> TL_EINVAL.
+ * Cleaning as in tl_graph_load; the ordering starts as the identity.
+ * On a union (from either call) tl_order_compute works part by part: part
+ * i's vertices get the ranks vbase_i + (their ranks in the part's own
+ * degree or Split ordering), so ranks [vbase_i, vbase_{i+1}) are part i's
+ * and a tl_list_triangles_range over them lists part i alone. */
+TL_EXPORT tl_status tl_graph_load_parts(tl_graph **out, uint32_t k, const uint32_t *n,
+                                        const uint64_t *m_in, const uint32_t *edges,
+                                        int edges_on_device, void *stream);
+
+/* tl_graph_union: the disjoint union of k >= 1 loaded graphs, each under
+ * rank[i] (device pointer, n_i part-local ranks) or, when rank or rank[i]
+ * is NULL, under its current ordering (the identity if none was applied).
+ * The union's ordering puts part i's vertex v at rank vbase_i + rank_i[v],
+ * so each part keeps its DAG G_pi and its costs; C++ and C+- of the union
+ * are the sums over parts (Sec. 3.1).  The DAG is built before returning.
+ * A rank[i] that is not a permutation of [0, n_i) -> TL_EINVAL.  The parts
+ * are only read, and must not be modified or freed during the call; they
+ * stay owned by the caller, and the union owns copies. */
+TL_EXPORT tl_status tl_graph_union(tl_graph **out, const tl_graph *const *graphs,
+                                   const uint32_t *const *rank, uint32_t k, void *stream);
+
 /* Number of vertices and of undirected edges (after cleaning). */
 TL_EXPORT tl_status tl_graph_size(const tl_graph *g, uint32_t *n, uint64_t *m);
 
@@ -99,7 +135,9 @@ TL_EXPORT tl_status tl_order_apply(tl_graph *g, const uint32_t *rank, int rank_o
  *                    non-increasing degree (ties by increasing id), the one at
  *                    1-based position 2i+1 gets pi = i+1, the one at 2i gets
  *                    pi = n+1-i.
- * The ordering is not applied; pass it to tl_order_apply. */
+ * On a disjoint union each part is ordered on its own (see
+ * tl_graph_load_parts).  The ordering is not applied; pass it to
+ * tl_order_apply. */
 typedef enum { TL_ORDER_DEGREE = 0, TL_ORDER_SPLIT = 1 } tl_order_kind;
 TL_EXPORT tl_status tl_order_compute(tl_graph *g, tl_order_kind kind, uint32_t *rank,
                                      int rank_on_device);
@@ -162,6 +200,28 @@ typedef struct {
 TL_EXPORT int tl_count_hash(const uint32_t *dev_triples, uint64_t n_triples,
                   uint64_t chunk_index, void *user);
 TL_EXPORT void tl_count_hash_release(tl_count_hash_state *s);
+
+/* The count + hash consumer per part of a disjoint union (tl_graph_load_parts,
+ * tl_graph_union): each triple (a, b, c) belongs to the part p with
+ * vbase[p] <= a < vbase[p+1] and is hashed with its part-local ids
+ * (a - vbase[p], b - vbase[p], c - vbase[p]) by the H of tl_count_hash, so a
+ * part's (count, hash) equals what tl_count_hash gives for that graph alone.
+ * The paper has no counterpart: this demultiplexes batched listing.
+ *   vbase   device, k+1 uint64 vertex offsets (vbase[0] = 0, vbase[k] = n).
+ *   counts  device, k uint64; each call adds the chunk's per-part counts.
+ *   hashes  device, k uint64; each call adds the chunk's per-part hashes.
+ * All three are caller-owned (zero counts and hashes before listing); the
+ * consumer allocates nothing.  The reduction runs on `stream` and is
+ * synchronised before the call returns.  Returns 0 on success. */
+typedef struct {
+  const uint64_t *vbase; /* in: device */
+  uint32_t k;            /* in: number of parts (>= 1) */
+  uint64_t *counts;      /* in/out: device */
+  uint64_t *hashes;      /* in/out: device */
+  void *stream;          /* in: cudaStream_t for the reduction (NULL = default) */
+} tl_count_hash_parts_state;
+TL_EXPORT int tl_count_hash_parts(const uint32_t *dev_triples, uint64_t n_triples,
+                                  uint64_t chunk_index, void *user);
 
 /* The count + hash consumer again, for callers that cannot allocate device
  * memory.  The paper has no counterpart: this is a library convenience.

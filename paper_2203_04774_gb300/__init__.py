@@ -42,6 +42,10 @@ class CountHashNoallocState(ctypes.Structure):
 TL_NOALLOC_MAX_TRIPLES = 1 << 28
 
 
+class CountHashPartsState(ctypes.Structure):
+    _fields_ = [("vbase", _P), ("k", _U32), ("counts", _P), ("hashes", _P), ("stream", _P)]
+
+
 class ListStats(ctypes.Structure):
     _fields_ = [("launches", _U64), ("chunks", _U64), ("triangles", _U64), ("probes", _U64),
                 ("tasks", _U64 * 4), ("kernel_ms", ctypes.c_double * 4),
@@ -50,6 +54,8 @@ class ListStats(ctypes.Structure):
 
 SIGNATURES = {
     "tl_graph_load": ([ctypes.POINTER(_P), _U32, _P, _U64, _I, _P], _I),
+    "tl_graph_load_parts": ([ctypes.POINTER(_P), _U32, _P, _P, _P, _I, _P], _I),
+    "tl_graph_union": ([ctypes.POINTER(_P), _P, _P, _U32, _P], _I),
     "tl_graph_size": ([_P, ctypes.POINTER(_U32), ctypes.POINTER(_U64)], _I),
     "tl_order_apply": ([_P, _P, _I], _I),
     "tl_order_compute": ([_P, _I, _P, _I], _I),
@@ -61,6 +67,7 @@ SIGNATURES = {
     "tl_count_hash_release": ([ctypes.POINTER(CountHashState)], None),
     "tl_graph_csr": ([_P, _I, _P, _P], _I),
     "tl_count_hash_noalloc": ([_P, _U64, _U64, _P], _I),
+    "tl_count_hash_parts": ([_P, _U64, _U64, _P], _I),
     "tl_last_list_stats": ([_P, ctypes.POINTER(ListStats)], _I),
     "tl_kernel_launches": ([], _U64),
     "tl_graph_free": ([_P], None),
@@ -132,6 +139,51 @@ def tl_graph_load(n: int, edges, stream=None) -> ctypes.c_void_p:
     h = _P()
     _check(lib().tl_graph_load(ctypes.byref(h), n, ptr, m_in, on_dev, _stream_handle(stream)),
            "tl_graph_load")
+    return h
+
+
+def tl_graph_load_parts(n, m_in, edges, stream=None) -> ctypes.c_void_p:
+    """Disjoint union of k graphs from one concatenated pair list with part-local ids.
+
+    ``n`` and ``m_in`` are sequences of k part sizes and pair counts; ``edges``
+    holds the parts' pairs one part after the other ([sum m_in, 2], host numpy
+    or device torch)."""
+    nn = np.ascontiguousarray(n, dtype=np.uint32)
+    mm = np.ascontiguousarray(m_in, dtype=np.uint64)
+    if nn.shape != mm.shape or nn.ndim != 1:
+        raise ValueError("n and m_in must be 1-d sequences of equal length")
+    ptr, on_dev, keep = _ptr_and_flag(edges)
+    if int(np.prod(keep.shape)) != 2 * int(mm.sum()):
+        raise ValueError("edges must hold 2 * sum(m_in) ids")
+    h = _P()
+    _check(lib().tl_graph_load_parts(ctypes.byref(h), len(nn), nn.ctypes.data, mm.ctypes.data,
+                                     ptr, on_dev, _stream_handle(stream)),
+           "tl_graph_load_parts")
+    return h
+
+
+def tl_graph_union(graphs, ranks=None, stream=None) -> ctypes.c_void_p:
+    """Disjoint union of loaded graphs (handles), each under ranks[i] (a device
+    torch uint32/int32 tensor of its n_i ranks) or its current ordering (None)."""
+    k = len(graphs)
+    harr = (_P * k)(*[g.value if isinstance(g, _P) else g for g in graphs])
+    keep = []
+    rarr = None
+    if ranks is not None:
+        if len(ranks) != k:
+            raise ValueError("ranks must have one entry per graph")
+        rarr = (_P * k)()
+        for i, r in enumerate(ranks):
+            if r is None:
+                continue
+            ptr, on_dev, kp = _ptr_and_flag(r)
+            if not on_dev:
+                raise ValueError("ranks must be device tensors")
+            keep.append(kp)
+            rarr[i] = ptr
+    h = _P()
+    _check(lib().tl_graph_union(ctypes.byref(h), harr, rarr, k, _stream_handle(stream)),
+           "tl_graph_union")
     return h
 
 
@@ -286,12 +338,83 @@ class CountHash:
         lib().tl_count_hash_release(ctypes.byref(self.state))
 
 
+class CountHashParts:
+    """The library's per-part count + hash consumer for a disjoint union.
+
+    ``sizes`` are the parts' vertex counts n_i; the offsets, counts and hashes
+    live in device tensors owned by this object."""
+
+    def __init__(self, sizes, stream=None, device="cuda"):
+        import torch
+        sizes = np.asarray(sizes, dtype=np.int64)
+        vb = np.zeros(len(sizes) + 1, dtype=np.int64)
+        np.cumsum(sizes, out=vb[1:])
+        self.vbase = torch.as_tensor(vb, device=device)
+        self.counts = torch.zeros(len(sizes), dtype=torch.int64, device=device)
+        self.hashes = torch.zeros(len(sizes), dtype=torch.int64, device=device)
+        self.state = CountHashPartsState(self.vbase.data_ptr(), len(sizes),
+                                         self.counts.data_ptr(), self.hashes.data_ptr(),
+                                         _stream_handle(stream))
+
+    @property
+    def user(self):
+        return ctypes.cast(ctypes.pointer(self.state), _P)
+
+    @staticmethod
+    def fn() -> int:
+        return ctypes.cast(lib().tl_count_hash_parts, _P).value
+
+    def reset(self):
+        self.counts.zero_()
+        self.hashes.zero_()
+
+    def results(self) -> tuple[np.ndarray, np.ndarray]:
+        """(counts, hashes) as uint64 numpy arrays, one entry per part."""
+        return (self.counts.cpu().numpy().view(np.uint64).copy(),
+                self.hashes.cpu().numpy().view(np.uint64).copy())
+
+
 class Graph:
     """A graph handle: load, order, cost, list (thin wrapper over tl_*)."""
 
     def __init__(self, n: int, edges, stream=None):
         self.n = n
         self.h = tl_graph_load(n, edges, stream)
+
+    @classmethod
+    def _wrap(cls, h) -> "Graph":
+        g = cls.__new__(cls)
+        g.h = h
+        g.n = tl_graph_size(h)[0]
+        return g
+
+    @classmethod
+    def load_parts(cls, n, m_in, edges, stream=None) -> "Graph":
+        """Disjoint union of graphs given as one concatenated pair list."""
+        return cls._wrap(tl_graph_load_parts(n, m_in, edges, stream))
+
+    @classmethod
+    def union(cls, graphs, ranks=None, stream=None) -> "Graph":
+        """Disjoint union of Graph objects under the given (or current) orderings."""
+        return cls._wrap(tl_graph_union([g.h for g in graphs], ranks, stream))
+
+    def order_compute(self, kind: int, rank=None):
+        """Device ordering (TL_ORDER_DEGREE / TL_ORDER_SPLIT) as ranks; a new
+        CUDA int32 tensor unless ``rank`` is given."""
+        if rank is None:
+            import torch
+            rank = torch.empty(self.n, dtype=torch.int32, device="cuda")
+        return tl_order_compute(self.h, kind, rank)
+
+    def list_count_hash_parts(self, alg: int, sizes, chunk_bytes: int = TL_MIN_CHUNK_BYTES,
+                              x_begin: int = 0, x_end: int | None = None, stream=None):
+        """(triangles, per-part counts, per-part hashes, probes) of a union."""
+        ch = CountHashParts(sizes, stream)
+        nt, npb = tl_list_triangles_range(self.h, alg, x_begin,
+                                          self.n if x_end is None else x_end, chunk_bytes,
+                                          ch.fn(), ch.user)
+        c, h = ch.results()
+        return nt, c, h, npb
 
     def __del__(self):
         self.free()

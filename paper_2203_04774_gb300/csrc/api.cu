@@ -4,6 +4,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "list.cuh"
 
@@ -382,6 +383,56 @@ tl_status tl_graph_load(tl_graph **out, uint32_t n, const uint32_t *edges, uint6
   TL_API_END
 }
 
+tl_status tl_graph_load_parts(tl_graph **out, uint32_t k, const uint32_t *n,
+                              const uint64_t *m_in, const uint32_t *edges, int edges_on_device,
+                              void *stream) {
+  TL_API_BEGIN
+  if (!out) tl::fail(TL_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (k == 0 || !n || !m_in) tl::fail(TL_EINVAL, "k must be >= 1 and n, m_in non-NULL");
+  uint64_t total = 0;
+  for (uint32_t i = 0; i < k; ++i) {
+    if (n[i] == 0) tl::fail(TL_EINVAL, "every part needs n >= 1");
+    total += m_in[i];
+  }
+  if (total > 0 && !edges) tl::fail(TL_EINVAL, "edges is NULL");
+  require_device();
+  tl_graph *G = new tl_graph();
+  try {
+    G->bind(static_cast<cudaStream_t>(stream));
+    tl::build_edge_set_parts(G->g, k, n, m_in, edges, edges_on_device != 0);
+  } catch (...) {
+    delete G;
+    throw;
+  }
+  *out = G;
+  TL_API_END
+}
+
+tl_status tl_graph_union(tl_graph **out, const tl_graph *const *graphs,
+                         const uint32_t *const *rank, uint32_t k, void *stream) {
+  TL_API_BEGIN
+  if (!out) tl::fail(TL_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (k == 0 || !graphs) tl::fail(TL_EINVAL, "k must be >= 1 and graphs non-NULL");
+  std::vector<const tl::DeviceGraph *> parts(k);
+  for (uint32_t i = 0; i < k; ++i) {
+    if (!graphs[i]) tl::fail(TL_EINVAL, "a graph is NULL");
+    parts[i] = &graphs[i]->g;
+  }
+  require_device();
+  tl_graph *G = new tl_graph();
+  try {
+    G->bind(static_cast<cudaStream_t>(stream));
+    tl::build_union(G->g, k, parts.data(), rank);
+  } catch (...) {
+    delete G;
+    throw;
+  }
+  *out = G;
+  TL_API_END
+}
+
 tl_status tl_graph_size(const tl_graph *G, uint32_t *n, uint64_t *m) {
   TL_API_BEGIN
   if (!G) tl::fail(TL_EINVAL, "graph is NULL");
@@ -450,6 +501,27 @@ int tl_count_hash(const uint32_t *dev_triples, uint64_t n_triples, uint64_t chun
   }
   st->count += n_triples;
   st->hash += h;
+  return 0;
+}
+
+int tl_count_hash_parts(const uint32_t *dev_triples, uint64_t n_triples, uint64_t chunk_index,
+                        void *user) {
+  (void)chunk_index;
+  tl_count_hash_parts_state *st = static_cast<tl_count_hash_parts_state *>(user);
+  if (!st || !st->vbase || st->k == 0 || !st->counts || !st->hashes) {
+    tl::set_error("tl_count_hash_parts: state needs vbase, k >= 1, counts and hashes");
+    return 1;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(st->stream);
+  try {
+    tl::launch_count_hash_parts(dev_triples, n_triples, st->vbase, st->k,
+                                reinterpret_cast<unsigned long long *>(st->counts),
+                                reinterpret_cast<unsigned long long *>(st->hashes), s);
+    TL_CUDA(cudaStreamSynchronize(s));
+  } catch (const tl::Error &e) {
+    tl::set_error(e.msg);
+    return 1;
+  }
   return 0;
 }
 

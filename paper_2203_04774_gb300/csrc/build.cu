@@ -192,6 +192,38 @@ __global__ void k_ranks_from_sequence(const uint64_t *__restrict__ keys, uint32_
   }
 }
 
+// Part-wise orderings of a disjoint union.  keys[p] (low half v, sorted by the
+// ordering's sort value) -> part(v) << 32 | v, so that a stable sort on the
+// high half groups the parts in order and keeps each part's sequence.
+__global__ void k_part_keys(uint64_t *__restrict__ keys, uint32_t n,
+                            const uint64_t *__restrict__ vbase, uint32_t k) {
+  for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < n;
+       p += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t v = (uint32_t)keys[p];
+    uint32_t lo = 0, hi = k - 1;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi + 1) >> 1;
+      if (vbase[mid] <= v) lo = mid; else hi = mid - 1;
+    }
+    keys[p] = (uint64_t)lo << 32 | v;
+  }
+}
+
+// As k_ranks_from_sequence, within each part: the vertex at position p of
+// part i's sequence (p counted from vbase[i]) gets rank vbase[i] + r(p, n_i).
+__global__ void k_part_ranks(const uint64_t *__restrict__ keys, uint32_t n, int split,
+                             const uint64_t *__restrict__ vbase, uint32_t *__restrict__ rank) {
+  for (uint64_t q = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; q < n;
+       q += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t key = keys[q];
+    const uint32_t v = (uint32_t)key, part = (uint32_t)(key >> 32);
+    const uint64_t b = vbase[part], np = vbase[part + 1] - b, p = q - b;
+    uint64_t r = p;
+    if (split) r = (p % 2 == 0) ? p / 2 : np - (p + 1) / 2;
+    rank[v] = (uint32_t)(b + r);
+  }
+}
+
 template <class T>
 T read_scalar(const T *dev, cudaStream_t s) {
   T v;
@@ -222,11 +254,18 @@ void build_edge_set(DeviceGraph &g, const uint32_t *edges, uint64_t m_in, bool o
   }
   g.keys_a.reserve(m_in * 8);
   g.keys_b.reserve(m_in * 8);
-  uint64_t *ka = g.keys_a.as<uint64_t>(), *kb = g.keys_b.as<uint64_t>();
+  uint64_t *ka = g.keys_a.as<uint64_t>();
   k_canon<<<grid_for(m_in, kThreads), kThreads, 0, s>>>(dev_edges, m_in, n, ka, bad);
   TL_CHECK_LAUNCH();
   if (read_scalar(bad, s)) fail(TL_EINVAL, "tl_graph_load: an edge has an id >= n");
   staged.release();
+  finish_edge_set(g, m_in);
+}
+
+void finish_edge_set(DeviceGraph &g, uint64_t m_in) {
+  cudaStream_t s = g.stream;
+  const uint32_t n = g.n;
+  uint64_t *ka = g.keys_a.as<uint64_t>(), *kb = g.keys_b.as<uint64_t>();
   const int b = bits_for(n > 1 ? n - 1 : 1);
   radix_sort_u64(ka, kb, m_in, 0, b, 32, b, g.sort_tmp, g.scan_tmp, s);
   // unique (flags in kb's storage as uint32, positions after them)
@@ -243,6 +282,9 @@ void build_edge_set(DeviceGraph &g, const uint32_t *edges, uint64_t m_in, bool o
   TL_CHECK_LAUNCH();
   TL_CUDA(cudaStreamSynchronize(s));
   g.m = m;
+  g.keys_a.release();
+  g.keys_b.release();
+  g.sort_tmp.release();
 }
 
 void build_dag(DeviceGraph &g, const uint32_t *rank, bool on_device) {
@@ -327,6 +369,10 @@ void build_dag(DeviceGraph &g, const uint32_t *rank, bool on_device) {
   g.max_out_deg = (uint32_t)h[2];
   g.max_in_deg = (uint32_t)h[3];
   g.ordered = true;
+  // The sort buffers are dead until the next build; hand them back to the pool.
+  g.keys_a.release();
+  g.keys_b.release();
+  g.sort_tmp.release();
 }
 
 }  // namespace tl
@@ -358,9 +404,26 @@ void compute_order(DeviceGraph &g, int kind, uint32_t *rank, bool on_device) {
     out.reserve((uint64_t)n * 4);
     dst = out.as<uint32_t>();
   }
-  k_ranks_from_sequence<<<grid_for(n, kThreads), kThreads, 0, s>>>(ka.as<uint64_t>(), n, split,
-                                                                   dst);
-  TL_CHECK_LAUNCH();
+  const uint32_t k = g.part_vbase.size() > 2 ? (uint32_t)(g.part_vbase.size() - 1) : 1;
+  if (k > 1) {  // a union: the same ordering inside every part
+    DevBuf vb(s);
+    vb.reserve((uint64_t)(k + 1) * 8);
+    TL_CUDA(cudaMemcpyAsync(vb.p, g.part_vbase.data(), (uint64_t)(k + 1) * 8,
+                            cudaMemcpyHostToDevice, s));
+    k_part_keys<<<grid_for(n, kThreads), kThreads, 0, s>>>(ka.as<uint64_t>(), n,
+                                                           vb.as<uint64_t>(), k);
+    TL_CHECK_LAUNCH();
+    radix_sort_u64(ka.as<uint64_t>(), kb.as<uint64_t>(), n, 0, 0, 32, bits_for(k - 1), tmp, scan,
+                   s);
+    k_part_ranks<<<grid_for(n, kThreads), kThreads, 0, s>>>(ka.as<uint64_t>(), n, split,
+                                                            vb.as<uint64_t>(), dst);
+    TL_CHECK_LAUNCH();
+    TL_CUDA(cudaStreamSynchronize(s));  // vb is read by the kernels above
+  } else {
+    k_ranks_from_sequence<<<grid_for(n, kThreads), kThreads, 0, s>>>(ka.as<uint64_t>(), n,
+                                                                     split, dst);
+    TL_CHECK_LAUNCH();
+  }
   if (!on_device)
     TL_CUDA(cudaMemcpyAsync(rank, dst, (uint64_t)n * 4, cudaMemcpyDeviceToHost, s));
   TL_CUDA(cudaStreamSynchronize(s));

@@ -1,6 +1,8 @@
 // The device-resident graph and the internal entry points of each step.
 #pragma once
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace tl {
@@ -20,6 +22,9 @@ struct DeviceGraph {
   DevBuf keys_a, keys_b, sort_tmp, scan_tmp, small;  // small: flags/counters
   uint64_t cost_app = 0, cost_apm = 0;
   uint32_t max_out_deg = 0, max_in_deg = 0;
+  // A disjoint union's part table: part i holds vertices [vbase[i], vbase[i+1]);
+  // empty for a graph loaded whole.
+  std::vector<uint64_t> part_vbase;
   // Order every buffer's allocation and release on stream s.
   void bind(cudaStream_t s) {
     stream = s;
@@ -31,10 +36,23 @@ struct DeviceGraph {
 
 // a1: copy + canonicalise + dedup (build.cu).  Throws tl::Error.
 void build_edge_set(DeviceGraph &g, const uint32_t *edges, uint64_t m_in, bool on_device);
+// The tail of a1: sort the m_in canonical keys in g.keys_a (loops = ~0),
+// drop loops and duplicates into g.E, set g.m.
+void finish_edge_set(DeviceGraph &g, uint64_t m_in);
+// Disjoint unions (batch.cu).  Part i holds n[i] vertices and becomes
+// vertices [vbase[i], vbase[i] + n[i]) of the union.
+//   Concatenated edge lists with part-local ids (host arrays n, m_in of k entries).
+void build_edge_set_parts(DeviceGraph &g, uint32_t k, const uint32_t *n, const uint64_t *m_in,
+                          const uint32_t *edges, bool on_device);
+//   Loaded graphs, each under rank[i] (device, part-local) or, if null, its
+//   current ordering (identity when none was applied); builds the union's DAG.
+void build_union(DeviceGraph &u, uint32_t k, const DeviceGraph *const *parts,
+                 const uint32_t *const *rank);
 // a2-a5: validate the permutation, relabel, orient, CSR out/in, cost.
 // rank == nullptr applies the identity ordering.
 void build_dag(DeviceGraph &g, const uint32_t *rank, bool on_device);
-// Degree (kind 0) or Split (kind 1) ordering of the loaded graph into rank[n].
+// Degree (kind 0) or Split (kind 1) ordering of the loaded graph into rank[n];
+// on a union, part by part (part i's ranks are vbase[i] + its own ranks).
 void compute_order(DeviceGraph &g, int kind, uint32_t *rank, bool on_device);
 
 }  // namespace tl

@@ -665,6 +665,49 @@ __global__ void k_count_hash(const uint32_t *__restrict__ t, uint64_t n,
   if ((threadIdx.x & 31) == 0) atomicAdd(acc, h);
 }
 
+// Per-part count and set hash of a disjoint union's triples: a triple's part
+// is the one whose vertex range [vbase[p], vbase[p+1]) holds its ids, and it is
+// hashed with part-local ids, so a part's (count, H) is the one it has alone.
+// A warp whose 32 triples share one part adds them with one atomic pair.
+__global__ void k_count_hash_parts(const uint32_t *__restrict__ t, uint64_t n,
+                                   const uint64_t *__restrict__ vbase, uint32_t k,
+                                   unsigned long long *__restrict__ counts,
+                                   unsigned long long *__restrict__ hashes) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t w0 = blockIdx.x * (uint64_t)blockDim.x + (threadIdx.x & ~31u); w0 < n;
+       w0 += stride) {
+    const uint64_t i = w0 + lane;
+    const bool valid = i < n;
+    uint32_t p = 0xffffffffu;
+    unsigned long long h = 0;
+    if (valid) {
+      const uint32_t a = __ldcs(t + 3 * i), b = __ldcs(t + 3 * i + 1), c = __ldcs(t + 3 * i + 2);
+      uint32_t lo = 0, hi = k - 1;
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (__ldg(vbase + mid) <= a) lo = mid; else hi = mid - 1;
+      }
+      p = lo;
+      const uint32_t o = (uint32_t)__ldg(vbase + p);
+      h = triple_hash(a - o, b - o, c - o);
+    }
+    const uint32_t p0 = __shfl_sync(0xffffffffu, p, 0);
+    if (__all_sync(0xffffffffu, !valid || p == p0)) {
+      const unsigned cnt = __popc(__ballot_sync(0xffffffffu, valid));
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) h += __shfl_down_sync(0xffffffffu, h, d);
+      if (lane == 0) {
+        atomicAdd(counts + p0, (unsigned long long)cnt);
+        atomicAdd(hashes + p0, h);
+      }
+    } else if (valid) {
+      atomicAdd(counts + p, 1ull);
+      atomicAdd(hashes + p, h);
+    }
+  }
+}
+
 template <class K>
 int occupancy_grid(K kernel, int threads, int smem) {
   if (smem > 48 * 1024)
@@ -746,6 +789,14 @@ void launch_list(int tier, const ListArgs &a, cudaStream_t s) {
 void launch_count_hash(const uint32_t *t, uint64_t n, unsigned long long *acc, cudaStream_t s) {
   if (n == 0) return;
   k_count_hash<<<grid_for(n, 256), 256, 0, s>>>(t, n, acc);
+  TL_CHECK_LAUNCH();
+}
+
+void launch_count_hash_parts(const uint32_t *t, uint64_t n, const uint64_t *vbase, uint32_t k,
+                             unsigned long long *counts, unsigned long long *hashes,
+                             cudaStream_t s) {
+  if (n == 0) return;
+  k_count_hash_parts<<<grid_for(n, 256), 256, 0, s>>>(t, n, vbase, k, counts, hashes);
   TL_CHECK_LAUNCH();
 }
 

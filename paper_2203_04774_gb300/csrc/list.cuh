@@ -119,5 +119,8 @@ void launch_task_owner(const uint64_t *piece_prefix, uint32_t x_begin, uint64_t 
 void launch_list(int tier, const ListArgs &a, cudaStream_t s);
 int tier_grid(int tier);
 void launch_count_hash(const uint32_t *t, uint64_t n, unsigned long long *acc, cudaStream_t s);
+void launch_count_hash_parts(const uint32_t *t, uint64_t n, const uint64_t *vbase, uint32_t k,
+                             unsigned long long *counts, unsigned long long *hashes,
+                             cudaStream_t s);
 
 }  // namespace tl

@@ -122,6 +122,23 @@ def chung_lu(n: int, avg_deg: float, gamma: float, seed: int) -> np.ndarray:
     return e
 
 
+def chung_lu_family(count: int, n_range: tuple[int, int], deg_range: tuple[float, float],
+                    gamma_range: tuple[float, float], seed: int) -> dict:
+    """Parameters of ``count`` independent Chung-Lu graphs: n log-uniform in
+    n_range (rounded), average degree and exponent uniform in their ranges,
+    and a distinct edge seed per graph (all from the counter generator under
+    ``seed``, streams 10-12).  Graph i is ``chung_lu(n[i], deg[i], gamma[i],
+    seeds[i])``."""
+    lo, hi = np.log(n_range[0]), np.log(n_range[1])
+    n = np.rint(np.exp(lo + (hi - lo) * counter_uniform(seed, 10, count))).astype(np.int64)
+    n = np.clip(n, n_range[0], n_range[1])
+    deg = deg_range[0] + (deg_range[1] - deg_range[0]) * counter_uniform(seed, 11, count)
+    gam = gamma_range[0] + (gamma_range[1] - gamma_range[0]) * counter_uniform(seed, 12, count)
+    seeds = (seed << 32) + np.arange(count, dtype=np.int64)
+    pairs = np.rint(n * deg / 2.0).astype(np.int64)
+    return {"n": n, "deg": deg, "gamma": gam, "seeds": seeds, "pairs": pairs}
+
+
 def rmat(scale: int, edge_factor: int, a: float, b: float, c: float,
          seed: int) -> np.ndarray:
     """R-MAT edge list (Chakrabarti, Zhan and Faloutsos, SDM 2004), uint32 [M, 2].
