@@ -228,6 +228,129 @@ def run_batch(args):
     ch.release()
 
 
+SERVE = {"workload": "serve-chunglu-poisson", "generator": "Chung-Lu family", "pool_graphs": 128,
+         "n_range": [1000, 5000000], "n_distribution": "log-uniform",
+         "avg_degree_range": [8, 64], "exponent_range": [2.1, 3.0], "seed": 5,
+         "orderings": ["degree"], "algorithms": ["A++", "A+-"],
+         "rates_per_s": [100, 1000, 10000], "requests_per_rate": 2000}
+
+
+def run_serve(args):
+    """Poisson stream of listing requests against the request server.
+
+    The pool graphs and their orderings are generated, loaded and registered
+    before timing (device resident).  For each arrival rate, the same request
+    sequence is served twice: batched (max_batch 256, 2 workers) and one
+    request per pass (max_batch 1, 1 worker).  Latency = scheduled arrival ->
+    completion on the server's clock; throughput = requests / (last completion
+    - first arrival).  Both modes must give every request the same result."""
+    import threading
+
+    import torch
+
+    import paper_2203_04774_gb300 as tl
+    from paper_2203_04774_gb300 import synth
+    from paper_2203_04774_gb300.synth import device as sdev
+
+    torch.cuda.set_device(0)
+    cfg = dict(SERVE)
+    if args.serve_requests:
+        cfg["requests_per_rate"] = args.serve_requests
+    fam = synth.chung_lu_family(cfg["pool_graphs"], cfg["n_range"], cfg["avg_degree_range"],
+                                cfg["exponent_range"], cfg["seed"])
+    t0 = time.time()
+    graphs, ranks, ms = [], [], []
+    for i in range(cfg["pool_graphs"]):
+        n = int(fam["n"][i])
+        e = sdev.chung_lu_device(n, float(fam["deg"][i]), float(fam["gamma"][i]),
+                                 int(fam["seeds"][i]))
+        g = tl.Graph(n, e)
+        del e
+        r = g.order_compute(tl.TL_ORDER_DEGREE)
+        graphs.append(g)
+        ranks.append([r])
+        ms.append(g.m)
+    torch.cuda.synchronize()
+    log(f"[bench] pool of {len(graphs)} graphs ready in {time.time() - t0:.1f}s: "
+        f"edges={sum(ms)}")
+    R = cfg["requests_per_rate"]
+    budget = 96 << 30
+
+    def requests(rate):
+        # counter-based draws under the workload seed: arrivals, graph, ordering, algorithm
+        gap = -np.log1p(-synth.counter_uniform(cfg["seed"], 20 + int(rate), R)) / rate
+        arr = np.cumsum(gap) - gap[0]
+        gi = (synth.counter_uniform(cfg["seed"], 30, R) * len(graphs)).astype(np.int64)
+        oi = np.zeros(R, np.int64)
+        al = (synth.counter_uniform(cfg["seed"], 31, R) < 0.5).astype(np.int64)
+        return arr, gi, oi, al
+
+    def serve(arr, gi, oi, al, max_batch, workers):
+        srv = tl.Server(budget, max_batch=max_batch, workers=workers)
+        ids = []
+        for g, rs in zip(graphs, ranks):
+            gid = srv.add_graph(g)
+            ids.append((gid, [srv.add_ordering(gid, r) for r in rs]))
+        rids = [None] * R
+        start = tl.Server.now_ns() + 20_000_000
+
+        def submitter():
+            for i in range(R):
+                target = start + int(arr[i] * 1e9)
+                while True:
+                    d = target - tl.Server.now_ns()
+                    if d <= 0:
+                        break
+                    if d > 2_000_000:
+                        time.sleep((d - 1_000_000) / 1e9)
+                rids[i] = srv.submit(ids[gi[i]][0], ids[gi[i]][1][oi[i]], int(al[i]))
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        th.join()
+        res = [srv.wait(r) for r in rids]
+        srv.close()
+        assert all(r["status"] == tl.TL_OK for r in res)
+        done = np.array([r["t_done_ns"] for r in res], np.float64)
+        sched = start + arr * 1e9
+        lat = (done - sched) / 1e9
+        span = (done.max() - sched.min()) / 1e9
+        tri = sum(r["triangles"] for r in res)
+        out = {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+               "requests_per_s": R / span, "triangles_per_s": tri / span,
+               "mean_batch": float(np.mean([r["batch_size"] for r in res])),
+               "max_batch_seen": int(max(r["batch_size"] for r in res))}
+        return out, [(r["triangles"], r["hash"]) for r in res]
+
+    clocks = Clocks(0)
+    clocks.start()
+    launches0 = tl.tl_kernel_launches()
+    rows = []
+    for rate in cfg["rates_per_s"]:
+        arr, gi, oi, al = requests(rate)
+        b, rb = serve(arr, gi, oi, al, 256, 2)
+        p, rp = serve(arr, gi, oi, al, 1, 1)
+        assert rb == rp, "a request's result depends on its batch"
+        rows.append({"rate_per_s": rate, "batched": b, "per_request": p,
+                     "throughput_ratio": b["requests_per_s"] / p["requests_per_s"]})
+        log(f"[bench] rate {rate}: batched {b} per-request {p}")
+    launches = tl.tl_kernel_launches() - launches0
+    clk = clocks.stop()
+    top = rows[-1]
+    line = {
+        "metric": "requests/s and p50/p99 latency, batched serving vs one request per pass",
+        "value": top["batched"]["requests_per_s"], "unit": "requests/s", "n_gpus": 1,
+        "steps": len(rows), "warmup": 0, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic (seeded Chung-Lu pool generated on the device, Poisson arrivals)",
+        "config": dict(cfg, pool_edges=int(sum(ms)), hbm_budget_bytes=budget,
+                       batched={"max_batch": 256, "workers": 2},
+                       per_request={"max_batch": 1, "workers": 1}),
+        "rates": rows, "equal_output": True, "gpu_launches": launches, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def read_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -579,12 +702,24 @@ def main():
                     help="R-MAT scale (20 is the measured workload; smaller for profiling)")
     ap.add_argument("--chunk-mb", type=int, default=DEFAULT_CHUNK_MB,
                     help="output chunk size in MiB")
-    ap.add_argument("--workload", default="rmat20", choices=sorted(WORKLOADS) + ["batch4096"],
+    ap.add_argument("--serve-requests", type=int, default=0,
+                    help="requests per arrival rate in the serve workload (default 2000)")
+    ap.add_argument("--workload", default="rmat20",
+                    choices=sorted(WORKLOADS) + ["batch4096", "serve"],
                     help="rmat20: the measured workload; chunglu1e8: the 2e9-edge graph; "
-                         "batch4096: 4096 graphs, batched vs one pass per graph")
+                         "batch4096: 4096 graphs, batched vs one pass per graph; "
+                         "serve: Poisson request stream, batched vs per-request")
     args = ap.parse_args()
     global CHUNK_BYTES, WORKLOAD
     CHUNK_BYTES = args.chunk_mb << 20
+    if args.workload == "serve":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the serving workload has no "
+                              "reference arm; its baseline is the per-request mode in the same "
+                              "line"}))
+        else:
+            run_serve(args)
+        return
     if args.workload == "batch4096":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the batched workload has no "

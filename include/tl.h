@@ -254,6 +254,73 @@ typedef struct {
 TL_EXPORT int tl_count_hash_noalloc(const uint32_t *dev_triples, uint64_t n_triples,
                                     uint64_t chunk_index, void *user);
 
+/* ---- Serving: listing requests over device-resident graphs ----------------
+ *
+ * The paper has no counterpart (it lists one graph at a time); this is the
+ * request loop around the same path.  Graphs and their orderings are
+ * registered once and stay on the device.  A request names a registered
+ * graph, one of its registered orderings and an algorithm (TL_APP or
+ * TL_APM), and gets back the count and set hash H (as tl_count_hash) of the
+ * graph's triangles.  Worker threads, one CUDA stream each, form batches:
+ * a worker takes the oldest waiting requests, as many as fit (at most
+ * max_batch, their estimated device footprint within what the budget has
+ * left), lists them as one disjoint union (tl_graph_union: A++ requests
+ * over the first rank range, A+- requests over the rest) and completes them
+ * together.  With workers >= 2, requests that arrive while one batch is on
+ * the GPU are admitted into the next as soon as a worker and memory are
+ * free, and the two batches overlap on the device.  max_batch = 1 serves
+ * one request per pass (the unbatched baseline).
+ *
+ * Footprint: a request on a graph with n vertices and m edges is charged
+ * 40 m + 160 n bytes (its share of the union's edge set, sort buffers,
+ * CSR and listing work arrays), and each batch the fixed buffers of one
+ * listing call (output chunks and staging).  A request that cannot fit in
+ * an empty server fails with TL_ENOMEM; otherwise it waits (first come,
+ * first served: a request never overtakes an older one).
+ *
+ * Thread safety: submit and wait may be called from any threads.  The
+ * registered graphs must stay alive, and must not be modified or freed,
+ * until tl_server_free returns; tl_server_free waits for every submitted
+ * request to finish. */
+typedef struct tl_server tl_server; /* opaque */
+typedef struct {
+  size_t hbm_budget_bytes; /* device bytes admitted batches may hold (estimate) */
+  uint32_t max_batch;      /* requests per batch, >= 1 */
+  uint32_t workers;        /* batches in flight, >= 1 (one host thread + stream each) */
+  size_t chunk_bytes;      /* output chunk of each listing, >= TL_MIN_CHUNK_BYTES */
+} tl_server_config;
+typedef struct {
+  tl_status status;      /* TL_OK, or why the request failed */
+  uint32_t batch_size;   /* requests listed in the same pass */
+  uint64_t triangles;    /* number of triangles of the graph */
+  uint64_t hash;         /* their set hash H */
+  uint64_t t_submit_ns;  /* tl_server_now_ns() at submit, admission and completion */
+  uint64_t t_admit_ns;
+  uint64_t t_done_ns;
+} tl_request_result;
+TL_EXPORT tl_status tl_server_create(tl_server **out, const tl_server_config *cfg);
+/* Register g (caller-owned, loaded on the current device) -> *graph_id. */
+TL_EXPORT tl_status tl_server_add_graph(tl_server *s, const tl_graph *g, uint32_t *graph_id);
+/* Register an ordering of a registered graph: rank[v] = pi_v - 1, n uint32,
+ * host or device pointer (copied).  Not a permutation -> TL_EINVAL. */
+TL_EXPORT tl_status tl_server_add_ordering(tl_server *s, uint32_t graph_id, const uint32_t *rank,
+                                           int rank_on_device, uint32_t *ordering_id);
+/* Queue a request; returns at once with its id. */
+TL_EXPORT tl_status tl_server_submit(tl_server *s, uint32_t graph_id, uint32_t ordering_id,
+                                     tl_alg alg, uint64_t *request_id);
+/* Block until the request has finished and return its result (each id can
+ * be waited for once).  An unknown id -> TL_EINVAL. */
+TL_EXPORT tl_status tl_server_wait(tl_server *s, uint64_t request_id, tl_request_result *out);
+/* Finish every submitted request, stop the workers, release the server's
+ * device memory.  NULL is a no-op. */
+TL_EXPORT void tl_server_free(tl_server *s);
+/* The admission charges: *request_bytes for one request on graph_id (may be
+ * NULL) and *batch_bytes for every batch (may be NULL). */
+TL_EXPORT tl_status tl_server_footprint(const tl_server *s, uint32_t graph_id,
+                                        uint64_t *request_bytes, uint64_t *batch_bytes);
+/* The monotonic clock of the result timestamps, in nanoseconds. */
+TL_EXPORT uint64_t tl_server_now_ns(void);
+
 /* Device copies of the DAG (rank space), for inspection and tests.
  *   dir 0: N+ (out) lists, dir 1: N- (in) lists.
  *   off: n+1 uint64 offsets, adj: m uint32 neighbour ranks, both host

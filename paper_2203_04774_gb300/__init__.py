@@ -46,6 +46,16 @@ class CountHashPartsState(ctypes.Structure):
     _fields_ = [("vbase", _P), ("k", _U32), ("counts", _P), ("hashes", _P), ("stream", _P)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", _SZ), ("max_batch", _U32), ("workers", _U32),
+                ("chunk_bytes", _SZ)]
+
+
+class RequestResult(ctypes.Structure):
+    _fields_ = [("status", _I), ("batch_size", _U32), ("triangles", _U64), ("hash", _U64),
+                ("t_submit_ns", _U64), ("t_admit_ns", _U64), ("t_done_ns", _U64)]
+
+
 class ListStats(ctypes.Structure):
     _fields_ = [("launches", _U64), ("chunks", _U64), ("triangles", _U64), ("probes", _U64),
                 ("tasks", _U64 * 4), ("kernel_ms", ctypes.c_double * 4),
@@ -66,6 +76,14 @@ SIGNATURES = {
     "tl_count_hash": ([_P, _U64, _U64, _P], _I),
     "tl_count_hash_release": ([ctypes.POINTER(CountHashState)], None),
     "tl_graph_csr": ([_P, _I, _P, _P], _I),
+    "tl_server_create": ([ctypes.POINTER(_P), ctypes.POINTER(ServerConfig)], _I),
+    "tl_server_add_graph": ([_P, _P, ctypes.POINTER(_U32)], _I),
+    "tl_server_add_ordering": ([_P, _U32, _P, _I, ctypes.POINTER(_U32)], _I),
+    "tl_server_submit": ([_P, _U32, _U32, _I, ctypes.POINTER(_U64)], _I),
+    "tl_server_wait": ([_P, _U64, ctypes.POINTER(RequestResult)], _I),
+    "tl_server_footprint": ([_P, _U32, ctypes.POINTER(_U64), ctypes.POINTER(_U64)], _I),
+    "tl_server_free": ([_P], None),
+    "tl_server_now_ns": ([], _U64),
     "tl_count_hash_noalloc": ([_P, _U64, _U64, _P], _I),
     "tl_count_hash_parts": ([_P, _U64, _U64, _P], _I),
     "tl_last_list_stats": ([_P, ctypes.POINTER(ListStats)], _I),
@@ -461,3 +479,64 @@ class Graph:
             return nt, int(ch.state.count), int(ch.state.hash), npb
         finally:
             ch.release()
+
+
+class Server:
+    """Request loop over device-resident graphs (tl_server_*): continuous
+    batching into disjoint unions, admission by estimated device footprint."""
+
+    def __init__(self, hbm_budget_bytes: int, max_batch: int = 256, workers: int = 2,
+                 chunk_bytes: int = 64 << 20):
+        cfg = ServerConfig(hbm_budget_bytes, max_batch, workers, chunk_bytes)
+        self.h = _P()
+        _check(lib().tl_server_create(ctypes.byref(self.h), ctypes.byref(cfg)),
+               "tl_server_create")
+        self._graphs = []  # registered graphs stay alive as long as the server
+
+    def add_graph(self, g: "Graph") -> int:
+        gid = _U32()
+        _check(lib().tl_server_add_graph(self.h, g.h, ctypes.byref(gid)), "tl_server_add_graph")
+        self._graphs.append(g)
+        return int(gid.value)
+
+    def add_ordering(self, graph_id: int, rank) -> int:
+        ptr, on_dev, keep = _ptr_and_flag(rank)
+        oid = _U32()
+        _check(lib().tl_server_add_ordering(self.h, graph_id, ptr, on_dev, ctypes.byref(oid)),
+               "tl_server_add_ordering")
+        return int(oid.value)
+
+    def footprint(self, graph_id: int) -> tuple[int, int]:
+        """(bytes charged per request on graph_id, bytes charged per batch)."""
+        r, b = _U64(), _U64()
+        _check(lib().tl_server_footprint(self.h, graph_id, ctypes.byref(r), ctypes.byref(b)),
+               "tl_server_footprint")
+        return int(r.value), int(b.value)
+
+    def submit(self, graph_id: int, ordering_id: int, alg: int) -> int:
+        rid = _U64()
+        _check(lib().tl_server_submit(self.h, graph_id, ordering_id, alg, ctypes.byref(rid)),
+               "tl_server_submit")
+        return int(rid.value)
+
+    def wait(self, request_id: int) -> dict:
+        r = RequestResult()
+        _check(lib().tl_server_wait(self.h, request_id, ctypes.byref(r)), "tl_server_wait")
+        return {"status": int(r.status), "batch_size": int(r.batch_size),
+                "triangles": int(r.triangles), "hash": int(r.hash),
+                "t_submit_ns": int(r.t_submit_ns), "t_admit_ns": int(r.t_admit_ns),
+                "t_done_ns": int(r.t_done_ns)}
+
+    @staticmethod
+    def now_ns() -> int:
+        return int(lib().tl_server_now_ns())
+
+    def close(self):
+        h = getattr(self, "h", None)
+        if h:
+            lib().tl_server_free(h)
+        self.h = None
+        self._graphs = []
+
+    def __del__(self):
+        self.close()

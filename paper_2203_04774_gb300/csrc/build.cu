@@ -287,6 +287,18 @@ void finish_edge_set(DeviceGraph &g, uint64_t m_in) {
   g.sort_tmp.release();
 }
 
+bool is_permutation(const uint32_t *rank, uint32_t n, uint32_t *flag, cudaStream_t s) {
+  DevBuf cnt(s);
+  cnt.reserve((uint64_t)n * 4);
+  TL_CUDA(cudaMemsetAsync(cnt.p, 0, (uint64_t)n * 4, s));
+  TL_CUDA(cudaMemsetAsync(flag, 0, 4, s));
+  k_rank_hist<<<grid_for(n, kThreads), kThreads, 0, s>>>(rank, n, cnt.as<uint32_t>(), flag);
+  TL_CHECK_LAUNCH();
+  k_rank_check<<<grid_for(n, kThreads), kThreads, 0, s>>>(cnt.as<uint32_t>(), n, flag);
+  TL_CHECK_LAUNCH();
+  return read_scalar(flag, s) == 0;
+}
+
 void build_dag(DeviceGraph &g, const uint32_t *rank, bool on_device) {
   cudaStream_t s = g.stream;
   const uint32_t n = g.n;
@@ -297,7 +309,7 @@ void build_dag(DeviceGraph &g, const uint32_t *rank, bool on_device) {
   TL_CUDA(cudaMemsetAsync(g.small.p, 0, 256, s));
 
   // a2: the ordering must be a permutation of [0, n).
-  DevBuf rank_new(s), cnt(s);
+  DevBuf rank_new(s);
   rank_new.reserve((uint64_t)n * 4);
   if (rank) {
     TL_CUDA(cudaMemcpyAsync(rank_new.p, rank, (uint64_t)n * 4,
@@ -306,15 +318,8 @@ void build_dag(DeviceGraph &g, const uint32_t *rank, bool on_device) {
     k_iota<<<grid_for(n, kThreads), kThreads, 0, s>>>(rank_new.as<uint32_t>(), n);
     TL_CHECK_LAUNCH();
   }
-  cnt.reserve((uint64_t)n * 4);
-  TL_CUDA(cudaMemsetAsync(cnt.p, 0, (uint64_t)n * 4, s));
-  k_rank_hist<<<grid_for(n, kThreads), kThreads, 0, s>>>(rank_new.as<uint32_t>(), n,
-                                                         cnt.as<uint32_t>(), bad);
-  TL_CHECK_LAUNCH();
-  k_rank_check<<<grid_for(n, kThreads), kThreads, 0, s>>>(cnt.as<uint32_t>(), n, bad);
-  TL_CHECK_LAUNCH();
-  if (read_scalar(bad, s)) fail(TL_EINVAL, "tl_order_apply: rank is not a permutation of [0, n)");
-  cnt.release();
+  if (!is_permutation(rank_new.as<uint32_t>(), n, bad, s))
+    fail(TL_EINVAL, "tl_order_apply: rank is not a permutation of [0, n)");
 
   g.rank.reserve((uint64_t)n * 4);
   g.inv.reserve((uint64_t)n * 4);

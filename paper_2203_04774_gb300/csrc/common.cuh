@@ -79,12 +79,13 @@ struct DevBuf {
 constexpr int kWarp = 32;
 
 inline int num_sms() {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
+  // initialised once, thread-safely (a throw leaves it for the next call)
+  static const int sms = [] {
+    int dev = 0, v = 0;
     TL_CUDA(cudaGetDevice(&dev));
-    TL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  }
+    TL_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev));
+    return v;
+  }();
   return sms;
 }
 

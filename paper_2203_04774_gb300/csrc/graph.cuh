@@ -48,6 +48,9 @@ void build_edge_set_parts(DeviceGraph &g, uint32_t k, const uint32_t *n, const u
 //   current ordering (identity when none was applied); builds the union's DAG.
 void build_union(DeviceGraph &u, uint32_t k, const DeviceGraph *const *parts,
                  const uint32_t *const *rank);
+// True iff rank[0..n) (device) is a permutation of [0, n); `flag` is one
+// device uint32 of scratch.  Synchronises s.
+bool is_permutation(const uint32_t *rank, uint32_t n, uint32_t *flag, cudaStream_t s);
 // a2-a5: validate the permutation, relabel, orient, CSR out/in, cost.
 // rank == nullptr applies the identity ordering.
 void build_dag(DeviceGraph &g, const uint32_t *rank, bool on_device);

@@ -761,15 +761,29 @@ void launch_task_owner(const uint64_t *piece_prefix, uint32_t x_begin, uint64_t 
 }
 
 int tier_grid(int tier) {
-  static int g[kTiers] = {0, 0, 0, 0};
-  if (!g[tier]) {
-    if (tier == 0) g[0] = occupancy_grid(k_list_warp<kSmallSlots>, kWarpThreads, kSmemSmall);
-    if (tier == 1) g[1] = occupancy_grid(k_list_warp<kMediumSlots>, kWarpThreads, kSmemMedium);
-    if (tier == 2) g[2] = occupancy_grid(k_list_cta<kMidThreads, 2>, kMidThreads, kSmemMid);
-    if (tier == 3)
-      g[3] = occupancy_grid(k_list_cta<kLargeThreads, 3>, kLargeThreads, kLargeSmemBytes);
+  // initialised once, thread-safely (a throw leaves it for the next call)
+  struct Grids {
+    int g[kTiers];
+  };
+  static const Grids grids = [] {
+    Grids r;
+    r.g[0] = occupancy_grid(k_list_warp<kSmallSlots>, kWarpThreads, kSmemSmall);
+    r.g[1] = occupancy_grid(k_list_warp<kMediumSlots>, kWarpThreads, kSmemMedium);
+    r.g[2] = occupancy_grid(k_list_cta<kMidThreads, 2>, kMidThreads, kSmemMid);
+    r.g[3] = occupancy_grid(k_list_cta<kLargeThreads, 3>, kLargeThreads, kLargeSmemBytes);
+    return r;
+  }();
+  return grids.g[tier];
+}
+
+uint64_t list_fixed_bytes(uint64_t chunk_bytes) {
+  uint64_t slab = 0;
+  for (int t = 0; t < kTiers; ++t) {
+    const uint64_t w = (uint64_t)tier_grid(t) * (t < 2 ? (kWarpThreads / 32) : 1) * slab_cap(t);
+    slab = w > slab ? w : slab;
   }
-  return g[tier];
+  return 2 * (chunk_bytes / 12) * 12 + slab * 12 +
+         (uint64_t)tier_grid(3) * kGHashSlots * 4;
 }
 
 void launch_list(int tier, const ListArgs &a, cudaStream_t s) {

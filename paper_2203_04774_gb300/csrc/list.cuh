@@ -118,6 +118,9 @@ void launch_task_owner(const uint64_t *piece_prefix, uint32_t x_begin, uint64_t 
 // tier 0, 1: warp kernels; tier 2: mid CTA kernel; tier 3: large CTA kernel.
 void launch_list(int tier, const ListArgs &a, cudaStream_t s);
 int tier_grid(int tier);
+// Device bytes one listing call holds whatever the graph: two output chunks,
+// the staging slabs and (at most) the hub hash tables.
+uint64_t list_fixed_bytes(uint64_t chunk_bytes);
 void launch_count_hash(const uint32_t *t, uint64_t n, unsigned long long *acc, cudaStream_t s);
 void launch_count_hash_parts(const uint32_t *t, uint64_t n, const uint64_t *vbase, uint32_t k,
                              unsigned long long *counts, unsigned long long *hashes,

@@ -1,0 +1,369 @@
+// Serving: a request loop with admission by device footprint and continuous
+// batching of requests into disjoint unions (declared in include/tl.h).
+//
+// Host code only.  Each worker thread owns a CUDA stream (plus one for the
+// consumer's reductions) and runs one batch at a time: union of the batch's
+// graphs under the requested orderings (tl_graph_union), one listing range per
+// algorithm, per-part count + hash (tl_count_hash_parts), results.  Workers
+// take requests from one FIFO queue under a mutex; admission charges an
+// estimated footprint against the budget and releases it when the batch ends.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "list.cuh"
+
+namespace {
+
+uint64_t now_ns() {
+  return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+struct Request {
+  uint64_t id = 0;
+  const tl_graph *g = nullptr;   // copied from the registry at submit, so that
+  const uint32_t *rank = nullptr;  // workers never read the registry
+  uint32_t n = 0;
+  tl_alg alg = TL_APP;
+  uint64_t footprint = 0;
+  bool done = false;
+  tl_request_result res{};
+};
+
+struct GraphEntry {
+  const tl_graph *g = nullptr;
+  uint32_t n = 0;
+  uint64_t m = 0;
+  std::vector<uint32_t *> ranks;  // device, n each, owned by the server
+};
+
+struct Worker {
+  std::thread th;
+  cudaStream_t stream = nullptr, cstream = nullptr;
+  uint64_t *d_vbase = nullptr, *d_counts = nullptr, *d_hashes = nullptr;  // max_batch (+1)
+};
+
+}  // namespace
+
+struct tl_server {
+  tl_server_config cfg{};
+  int device = 0;
+  uint64_t batch_fixed = 0;  // bytes one listing call holds whatever the graphs
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Request *> pending;
+  std::unordered_map<uint64_t, Request *> requests;
+  std::vector<GraphEntry> graphs;
+  uint64_t in_use = 0, next_id = 1;
+  bool stop = false;
+  std::vector<Worker> workers;
+};
+
+namespace {
+
+uint64_t footprint(uint32_t n, uint64_t m) { return 40 * m + 160 * (uint64_t)n; }
+
+// Runs one batch on worker W; fills every request's result (not `done`).
+void run_batch(tl_server *S, Worker &W, std::vector<Request *> &batch) {
+  std::stable_sort(batch.begin(), batch.end(),
+                   [](const Request *a, const Request *b) { return a->alg < b->alg; });
+  const uint32_t k = (uint32_t)batch.size();
+  std::vector<const tl_graph *> parts(k);
+  std::vector<const uint32_t *> ranks(k);
+  std::vector<uint64_t> vb(k + 1, 0);
+  uint32_t n_app = 0;
+  for (uint32_t i = 0; i < k; ++i) {
+    parts[i] = batch[i]->g;
+    ranks[i] = batch[i]->rank;
+    vb[i + 1] = vb[i] + batch[i]->n;
+    n_app += batch[i]->alg == TL_APP;
+  }
+  tl_status st = TL_OK;
+  std::vector<uint64_t> counts(k, 0), hashes(k, 0);
+  tl_graph *u = nullptr;
+  if (cudaSetDevice(S->device) != cudaSuccess) st = TL_ECUDA;
+  if (st == TL_OK) st = tl_graph_union(&u, parts.data(), ranks.data(), k, W.stream);
+  if (st == TL_OK) {
+    tl_count_hash_parts_state cs{W.d_vbase, k, W.d_counts, W.d_hashes, W.cstream};
+    bool ok = cudaMemcpyAsync(W.d_vbase, vb.data(), (k + 1) * 8, cudaMemcpyHostToDevice,
+                              W.cstream) == cudaSuccess &&
+              cudaMemsetAsync(W.d_counts, 0, k * 8, W.cstream) == cudaSuccess &&
+              cudaMemsetAsync(W.d_hashes, 0, k * 8, W.cstream) == cudaSuccess &&
+              cudaStreamSynchronize(W.cstream) == cudaSuccess;
+    if (!ok) st = TL_ECUDA;
+    const uint32_t split = (uint32_t)vb[n_app];
+    if (st == TL_OK && n_app > 0)
+      st = tl_list_triangles_range(u, TL_APP, 0, split, S->cfg.chunk_bytes, tl_count_hash_parts,
+                                   &cs, nullptr, nullptr);
+    if (st == TL_OK && n_app < k)
+      st = tl_list_triangles_range(u, TL_APM, split, (uint32_t)vb[k], S->cfg.chunk_bytes,
+                                   tl_count_hash_parts, &cs, nullptr, nullptr);
+    if (st == TL_OK) {
+      ok = cudaMemcpyAsync(counts.data(), W.d_counts, k * 8, cudaMemcpyDeviceToHost,
+                           W.cstream) == cudaSuccess &&
+           cudaMemcpyAsync(hashes.data(), W.d_hashes, k * 8, cudaMemcpyDeviceToHost,
+                           W.cstream) == cudaSuccess &&
+           cudaStreamSynchronize(W.cstream) == cudaSuccess;
+      if (!ok) st = TL_ECUDA;
+    }
+  }
+  if (u) tl_graph_free(u);
+  for (uint32_t i = 0; i < k; ++i) {
+    batch[i]->res.status = st;
+    batch[i]->res.batch_size = k;
+    batch[i]->res.triangles = st == TL_OK ? counts[i] : 0;
+    batch[i]->res.hash = st == TL_OK ? hashes[i] : 0;
+  }
+}
+
+void worker_main(tl_server *S, Worker *W) {
+  cudaSetDevice(S->device);
+  const uint64_t budget = S->cfg.hbm_budget_bytes;
+  for (;;) {
+    std::vector<Request *> batch;
+    uint64_t charged = 0;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      for (;;) {
+        if (S->pending.empty()) {
+          if (S->stop) return;
+          S->cv_work.wait(lk);
+          continue;
+        }
+        Request *head = S->pending.front();
+        if (head->footprint + S->batch_fixed > budget) {  // cannot fit even alone
+          S->pending.pop_front();
+          head->res.status = TL_ENOMEM;
+          head->res.t_admit_ns = head->res.t_done_ns = now_ns();
+          head->done = true;
+          S->cv_done.notify_all();
+          continue;
+        }
+        if (S->in_use + head->footprint + S->batch_fixed > budget) {
+          S->cv_work.wait(lk);  // wait for a batch to release memory
+          continue;
+        }
+        charged = S->batch_fixed;
+        while (!S->pending.empty() && batch.size() < S->cfg.max_batch) {
+          Request *r = S->pending.front();
+          if (S->in_use + charged + r->footprint > budget) break;
+          charged += r->footprint;
+          batch.push_back(r);
+          S->pending.pop_front();
+        }
+        S->in_use += charged;
+        break;
+      }
+    }
+    const uint64_t t_admit = now_ns();
+    for (Request *r : batch) r->res.t_admit_ns = t_admit;
+    run_batch(S, *W, batch);
+    const uint64_t t_done = now_ns();
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->in_use -= charged;
+      for (Request *r : batch) {
+        r->res.t_done_ns = t_done;
+        r->done = true;
+      }
+    }
+    S->cv_done.notify_all();
+    S->cv_work.notify_all();
+  }
+}
+
+void destroy(tl_server *S) {
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv_work.notify_all();
+  for (Worker &W : S->workers)
+    if (W.th.joinable()) W.th.join();
+  cudaSetDevice(S->device);
+  for (Worker &W : S->workers) {
+    if (W.d_vbase) cudaFree(W.d_vbase);
+    if (W.d_counts) cudaFree(W.d_counts);
+    if (W.d_hashes) cudaFree(W.d_hashes);
+    if (W.stream) cudaStreamDestroy(W.stream);
+    if (W.cstream) cudaStreamDestroy(W.cstream);
+  }
+  for (GraphEntry &ge : S->graphs)
+    for (uint32_t *r : ge.ranks) cudaFree(r);
+  for (auto &kv : S->requests) delete kv.second;
+  delete S;
+}
+
+}  // namespace
+
+#define TL_SERVE_BEGIN \
+  try {                \
+    tl::clear_error();
+#define TL_SERVE_END                              \
+  }                                               \
+  catch (const tl::Error &e) {                    \
+    tl::set_error(e.msg);                         \
+    return e.status;                              \
+  }                                               \
+  catch (const std::bad_alloc &) {                \
+    tl::set_error("host allocation failed");      \
+    return TL_ENOMEM;                             \
+  }                                               \
+  catch (...) {                                   \
+    tl::set_error("unexpected internal error");   \
+    return TL_ECUDA;                              \
+  }                                               \
+  return TL_OK;
+
+extern "C" {
+
+uint64_t tl_server_now_ns(void) { return now_ns(); }
+
+tl_status tl_server_create(tl_server **out, const tl_server_config *cfg) {
+  TL_SERVE_BEGIN
+  if (!out || !cfg) tl::fail(TL_EINVAL, "out or cfg is NULL");
+  *out = nullptr;
+  if (cfg->max_batch == 0 || cfg->workers == 0)
+    tl::fail(TL_EINVAL, "max_batch and workers must be >= 1");
+  if (cfg->chunk_bytes < TL_MIN_CHUNK_BYTES)
+    tl::fail(TL_EINVAL, "chunk_bytes below TL_MIN_CHUNK_BYTES");
+  tl_server *S = new tl_server();
+  S->cfg = *cfg;
+  try {
+    TL_CUDA(cudaGetDevice(&S->device));
+    S->batch_fixed = tl::list_fixed_bytes(cfg->chunk_bytes);
+    S->workers.resize(cfg->workers);
+    for (Worker &W : S->workers) {
+      TL_CUDA(cudaStreamCreateWithFlags(&W.stream, cudaStreamNonBlocking));
+      TL_CUDA(cudaStreamCreateWithFlags(&W.cstream, cudaStreamNonBlocking));
+      TL_CUDA(cudaMalloc(&W.d_vbase, ((uint64_t)cfg->max_batch + 1) * 8));
+      TL_CUDA(cudaMalloc(&W.d_counts, (uint64_t)cfg->max_batch * 8));
+      TL_CUDA(cudaMalloc(&W.d_hashes, (uint64_t)cfg->max_batch * 8));
+    }
+    for (Worker &W : S->workers) W.th = std::thread(worker_main, S, &W);
+  } catch (...) {
+    destroy(S);
+    throw;
+  }
+  *out = S;
+  TL_SERVE_END
+}
+
+tl_status tl_server_add_graph(tl_server *S, const tl_graph *g, uint32_t *graph_id) {
+  TL_SERVE_BEGIN
+  if (!S || !g || !graph_id) tl::fail(TL_EINVAL, "NULL argument");
+  GraphEntry ge;
+  ge.g = g;
+  tl_status st = tl_graph_size(g, &ge.n, &ge.m);
+  if (st != TL_OK) return st;
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->graphs.push_back(ge);
+  *graph_id = (uint32_t)(S->graphs.size() - 1);
+  TL_SERVE_END
+}
+
+tl_status tl_server_add_ordering(tl_server *S, uint32_t graph_id, const uint32_t *rank,
+                                 int rank_on_device, uint32_t *ordering_id) {
+  TL_SERVE_BEGIN
+  if (!S || !rank || !ordering_id) tl::fail(TL_EINVAL, "NULL argument");
+  uint32_t n = 0;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (graph_id >= S->graphs.size()) tl::fail(TL_EINVAL, "unknown graph_id");
+    n = S->graphs[graph_id].n;
+  }
+  TL_CUDA(cudaSetDevice(S->device));
+  uint32_t *d = nullptr;
+  cudaStream_t s = nullptr;
+  TL_CUDA(cudaMalloc(&d, (uint64_t)n * 4 + 4));  // + 4: the check's flag
+  try {
+    TL_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    TL_CUDA(cudaMemcpyAsync(d, rank, (uint64_t)n * 4,
+                            rank_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                            s));
+    if (!tl::is_permutation(d, n, d + n, s))
+      tl::fail(TL_EINVAL, "tl_server_add_ordering: rank is not a permutation of [0, n)");
+    cudaStreamDestroy(s);
+  } catch (...) {
+    if (s) {
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+    }
+    cudaFree(d);
+    throw;
+  }
+  std::lock_guard<std::mutex> lk(S->mu);
+  GraphEntry &ge = S->graphs[graph_id];
+  ge.ranks.push_back(d);
+  *ordering_id = (uint32_t)(ge.ranks.size() - 1);
+  TL_SERVE_END
+}
+
+tl_status tl_server_submit(tl_server *S, uint32_t graph_id, uint32_t ordering_id, tl_alg alg,
+                           uint64_t *request_id) {
+  TL_SERVE_BEGIN
+  if (!S || !request_id) tl::fail(TL_EINVAL, "NULL argument");
+  if (alg != TL_APP && alg != TL_APM) tl::fail(TL_EINVAL, "alg must be TL_APP or TL_APM");
+  Request *r = new Request();
+  r->res.t_submit_ns = now_ns();
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (graph_id >= S->graphs.size() || ordering_id >= S->graphs[graph_id].ranks.size()) {
+      delete r;
+      tl::fail(TL_EINVAL, "unknown graph_id or ordering_id");
+    }
+    const GraphEntry &ge = S->graphs[graph_id];
+    r->id = S->next_id++;
+    r->g = ge.g;
+    r->rank = ge.ranks[ordering_id];
+    r->n = ge.n;
+    r->alg = alg;
+    r->footprint = footprint(ge.n, ge.m);
+    S->requests[r->id] = r;
+    S->pending.push_back(r);
+    *request_id = r->id;
+  }
+  S->cv_work.notify_one();
+  TL_SERVE_END
+}
+
+tl_status tl_server_wait(tl_server *S, uint64_t request_id, tl_request_result *out) {
+  TL_SERVE_BEGIN
+  if (!S || !out) tl::fail(TL_EINVAL, "NULL argument");
+  std::unique_lock<std::mutex> lk(S->mu);
+  auto it = S->requests.find(request_id);
+  if (it == S->requests.end()) tl::fail(TL_EINVAL, "unknown request id");
+  Request *r = it->second;
+  S->cv_done.wait(lk, [r] { return r->done; });
+  *out = r->res;
+  S->requests.erase(it);
+  delete r;
+  TL_SERVE_END
+}
+
+tl_status tl_server_footprint(const tl_server *S, uint32_t graph_id, uint64_t *request_bytes,
+                              uint64_t *batch_bytes) {
+  TL_SERVE_BEGIN
+  if (!S) tl::fail(TL_EINVAL, "server is NULL");
+  tl_server *W = const_cast<tl_server *>(S);
+  std::lock_guard<std::mutex> lk(W->mu);
+  if (graph_id >= S->graphs.size()) tl::fail(TL_EINVAL, "unknown graph_id");
+  if (request_bytes) *request_bytes = footprint(S->graphs[graph_id].n, S->graphs[graph_id].m);
+  if (batch_bytes) *batch_bytes = S->batch_fixed;
+  TL_SERVE_END
+}
+
+void tl_server_free(tl_server *S) {
+  if (S) destroy(S);
+}
+
+}  // extern "C"

@@ -68,3 +68,18 @@ def test_no_device_is_an_error_not_a_fallback(built):
     h = ctypes.c_void_p()
     st = built.tl_graph_load(ctypes.byref(h), 3, e.ctypes.data, 3, 0, None)
     assert st == tl.TL_ECUDA
+
+
+def test_union_and_server_arguments_rejected_without_gpu(built):
+    h = ctypes.c_void_p()
+    n = (ctypes.c_uint32 * 2)(3, 0)
+    m = (ctypes.c_uint64 * 2)(0, 0)
+    assert built.tl_graph_load_parts(ctypes.byref(h), 0, n, m, None, 0, None) == tl.TL_EINVAL
+    assert built.tl_graph_load_parts(ctypes.byref(h), 2, n, m, None, 0, None) == tl.TL_EINVAL
+    assert built.tl_graph_union(ctypes.byref(h), None, None, 1, None) == tl.TL_EINVAL
+    for cfg in (tl.ServerConfig(1 << 30, 0, 1, 64 << 20), tl.ServerConfig(1 << 30, 8, 0, 64 << 20),
+                tl.ServerConfig(1 << 30, 8, 1, 1 << 20)):
+        assert built.tl_server_create(ctypes.byref(h), ctypes.byref(cfg)) == tl.TL_EINVAL
+    assert built.tl_server_create(ctypes.byref(h), None) == tl.TL_EINVAL
+    built.tl_server_free(None)
+    assert built.tl_count_hash_parts(None, 0, 0, None) != 0

@@ -1,0 +1,161 @@
+"""The request server (tl_server_*): every request's result equals the graph's
+own result alone and the oracle's, however requests are batched together;
+admission by footprint; argument errors.  Every call goes through the C ABI."""
+import threading
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2203_04774_gb300 as tl
+from paper_2203_04774_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+    import torch
+    torch.cuda.set_device(0)
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.fixture(scope="module")
+def pool():
+    """24 graphs of uneven size, two orderings each (degree; random or core),
+    with the oracle's (count, hash) for every (graph, ordering, algorithm)."""
+    rng = np.random.default_rng(5)
+    graphs = []
+    for i in range(24):
+        n = int(np.exp(rng.uniform(np.log(30), np.log(20000))))
+        e = synth.chung_lu(n, float(rng.uniform(4, 40)), float(rng.uniform(2.1, 3.0)), 500 + i)
+        off, adj = synth.simple_csr(n, e)
+        orders = [synth.order_degree(off),
+                  synth.order_core(off, adj) if i % 2 else synth.order_random(n, i)]
+        want = {}
+        ref = oracle.Graph(n, e)
+        for o, r in enumerate(orders):
+            ref.order_apply(r)
+            for alg in (tl.TL_APP, tl.TL_APM):
+                _, c, h, _ = ref.list(alg, store=False)
+                want[(o, alg)] = (c, h)
+        graphs.append((n, e, orders, want))
+    return graphs
+
+
+def _register(srv, pool):
+    ids = []
+    for n, e, orders, _ in pool:
+        g = tl.Graph(n, _dev(e))
+        gid = srv.add_graph(g)
+        oids = [srv.add_ordering(gid, _dev(r)) for r in orders]
+        ids.append((gid, oids))
+    return ids
+
+
+def _requests(pool, count, seed):
+    rng = np.random.default_rng(seed)
+    return [(int(rng.integers(len(pool))), int(rng.integers(2)),
+             tl.TL_APP if rng.random() < 0.5 else tl.TL_APM) for _ in range(count)]
+
+
+def _run(srv, ids, reqs):
+    rids = [srv.submit(ids[p][0], ids[p][1][o], a) for p, o, a in reqs]
+    return [srv.wait(r) for r in rids]
+
+
+@pytest.mark.parametrize("max_batch,workers", [(64, 2), (1, 1), (7, 3)])
+def test_every_request_matches_the_oracle_in_any_mix(pool, max_batch, workers):
+    srv = tl.Server(64 << 30, max_batch=max_batch, workers=workers)
+    ids = _register(srv, pool)
+    reqs = _requests(pool, 150, 1)
+    res = _run(srv, ids, reqs)
+    for (p, o, a), r in zip(reqs, res):
+        assert r["status"] == tl.TL_OK
+        assert (r["triangles"], r["hash"]) == pool[p][3][(o, a)], (p, o, a)
+        assert r["t_submit_ns"] <= r["t_admit_ns"] <= r["t_done_ns"]
+        assert 1 <= r["batch_size"] <= max_batch
+    sizes = [r["batch_size"] for r in res]
+    if max_batch > 1:
+        assert max(sizes) > 1  # requests submitted together were listed together
+    srv.close()
+
+
+def test_concurrent_clients(pool):
+    srv = tl.Server(64 << 30, max_batch=32, workers=2)
+    ids = _register(srv, pool)
+    out, errors = {}, []
+
+    def client(c):
+        try:
+            reqs = _requests(pool, 40, 100 + c)
+            out[c] = (reqs, _run(srv, ids, reqs))
+        except BaseException as e:  # surfaced below
+            errors.append(e)
+
+    threads = [threading.Thread(target=client, args=(c,)) for c in range(4)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    for reqs, res in out.values():
+        for (p, o, a), r in zip(reqs, res):
+            assert (r["status"], r["triangles"], r["hash"]) == (tl.TL_OK,) + pool[p][3][(o, a)]
+    srv.close()
+
+
+def test_admission_by_footprint(pool):
+    # a budget that holds one batch of the largest graph's request but not
+    # more: requests still all finish (they wait for memory), in order
+    probe = tl.Server(64 << 30, max_batch=64, workers=2)
+    ids = _register(probe, pool)
+    big = int(np.argmax([p[0] for p in pool]))
+    req_bytes, batch_bytes = probe.footprint(ids[big][0])
+    probe.close()
+    srv = tl.Server(batch_bytes + req_bytes, max_batch=64, workers=2)
+    ids = _register(srv, pool)
+    reqs = _requests(pool, 60, 2) + [(big, 0, tl.TL_APP)] * 3
+    res = _run(srv, ids, reqs)
+    for (p, o, a), r in zip(reqs, res):
+        assert (r["status"], r["triangles"], r["hash"]) == (tl.TL_OK,) + pool[p][3][(o, a)]
+    for r in res[-3:]:
+        assert r["batch_size"] == 1  # the largest request fills the budget alone
+    srv.close()
+    # a budget below one request of the largest graph: that request fails with
+    # TL_ENOMEM, smaller ones are served
+    srv = tl.Server(batch_bytes + req_bytes - 1, max_batch=64, workers=2)
+    ids = _register(srv, pool)
+    small = int(np.argmin([p[0] for p in pool]))
+    res = _run(srv, ids, [(big, 0, tl.TL_APM), (small, 1, tl.TL_APP)])
+    assert res[0]["status"] == tl.TL_ENOMEM
+    assert (res[1]["status"], res[1]["triangles"]) == (tl.TL_OK, pool[small][3][(1, tl.TL_APP)][0])
+    srv.close()
+
+
+def test_server_argument_errors(pool):
+    srv = tl.Server(8 << 30, max_batch=4, workers=1)
+    n, e, orders, _ = pool[0]
+    g = tl.Graph(n, _dev(e))
+    gid = srv.add_graph(g)
+    bad = orders[0].copy()
+    bad[0] = bad[1]
+    with pytest.raises(tl.TLError) as ei:
+        srv.add_ordering(gid, _dev(bad))
+    assert ei.value.status == tl.TL_EINVAL
+    oid = srv.add_ordering(gid, orders[0])  # host pointer
+    with pytest.raises(tl.TLError):
+        srv.submit(gid + 1, oid, tl.TL_APP)
+    with pytest.raises(tl.TLError):
+        srv.submit(gid, oid + 1, tl.TL_APP)
+    with pytest.raises(tl.TLError):
+        srv.wait(12345)
+    r = srv.wait(srv.submit(gid, oid, tl.TL_APP))
+    assert (r["triangles"], r["hash"]) == pool[0][3][(0, tl.TL_APP)]
+    srv.close()
