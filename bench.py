@@ -231,7 +231,8 @@ def run_batch(args):
 SERVE = {"workload": "serve-chunglu-poisson", "generator": "Chung-Lu family", "pool_graphs": 128,
          "n_range": [1000, 5000000], "n_distribution": "log-uniform",
          "avg_degree_range": [8, 64], "exponent_range": [2.1, 3.0], "seed": 5,
-         "orderings": ["degree"], "algorithms": ["A++", "A+-"],
+         "orderings": ["degree", "core (level-synchronous peeling)"],
+         "algorithms": ["A++", "A+-"],
          "rates_per_s": [100, 1000, 10000], "requests_per_rate": 2000}
 
 
@@ -266,9 +267,8 @@ def run_serve(args):
                                  int(fam["seeds"][i]))
         g = tl.Graph(n, e)
         del e
-        r = g.order_compute(tl.TL_ORDER_DEGREE)
         graphs.append(g)
-        ranks.append([r])
+        ranks.append([g.order_compute(tl.TL_ORDER_DEGREE), g.order_compute(tl.TL_ORDER_CORE)])
         ms.append(g.m)
     torch.cuda.synchronize()
     log(f"[bench] pool of {len(graphs)} graphs ready in {time.time() - t0:.1f}s: "
@@ -281,7 +281,7 @@ def run_serve(args):
         gap = -np.log1p(-synth.counter_uniform(cfg["seed"], 20 + int(rate), R)) / rate
         arr = np.cumsum(gap) - gap[0]
         gi = (synth.counter_uniform(cfg["seed"], 30, R) * len(graphs)).astype(np.int64)
-        oi = np.zeros(R, np.int64)
+        oi = (synth.counter_uniform(cfg["seed"], 32, R) < 0.5).astype(np.int64)
         al = (synth.counter_uniform(cfg["seed"], 31, R) < 0.5).astype(np.int64)
         return arr, gi, oi, al
 

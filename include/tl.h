@@ -134,11 +134,20 @@ TL_EXPORT tl_status tl_order_apply(tl_graph *g, const uint32_t *rank, int rank_o
  *   TL_ORDER_SPLIT:  the Split heuristic of Sec. 3.3.3 -- vertices by
  *                    non-increasing degree (ties by increasing id), the one at
  *                    1-based position 2i+1 gets pi = i+1, the one at 2i gets
- *                    pi = n+1-i.
+ *                    pi = n+1-i;
+ *   TL_ORDER_CORE:   a core ordering (Sec. 1.3, Sec. 2.2) by level-synchronous
+ *                    peeling: at level k every remaining vertex of degree
+ *                    <= k is removed in one round, the neighbours whose degree
+ *                    falls to k in the next round, and so on; then k moves to
+ *                    the smallest remaining degree.  Vertices are ranked by
+ *                    (round, id): coreness is non-decreasing along the
+ *                    ordering and d+_v <= c_v for every v (a degeneracy
+ *                    ordering).  Ties differ from one-vertex-at-a-time
+ *                    peeling (Batagelj and Zaversnik).
  * On a disjoint union each part is ordered on its own (see
  * tl_graph_load_parts).  The ordering is not applied; pass it to
  * tl_order_apply. */
-typedef enum { TL_ORDER_DEGREE = 0, TL_ORDER_SPLIT = 1 } tl_order_kind;
+typedef enum { TL_ORDER_DEGREE = 0, TL_ORDER_SPLIT = 1, TL_ORDER_CORE = 2 } tl_order_kind;
 TL_EXPORT tl_status tl_order_compute(tl_graph *g, tl_order_kind kind, uint32_t *rank,
                                      int rank_on_device);
 

@@ -157,3 +157,90 @@ def canonical(triples: np.ndarray) -> np.ndarray:
     t = np.sort(t, axis=1)
     order = np.lexsort((t[:, 2], t[:, 1], t[:, 0]))
     return t[order]
+
+
+def core_numbers(n: int, edges: np.ndarray) -> np.ndarray:
+    """Coreness c_v of every vertex (Sec. 1.3: the largest k such that v lies
+    in a subgraph whose vertices all have degree >= k), by the plain
+    peeling argument: repeatedly delete a vertex of minimum remaining
+    degree; c_v is the largest minimum degree seen up to v's deletion.
+    Pure Python with a lazy heap -- small graphs only."""
+    import heapq
+    e = np.asarray(edges, dtype=np.int64).reshape(-1, 2)
+    e = e[e[:, 0] != e[:, 1]]
+    lo, hi = np.minimum(e[:, 0], e[:, 1]), np.maximum(e[:, 0], e[:, 1])
+    pairs = np.unique(lo * n + hi)
+    adj = [[] for _ in range(n)]
+    for key in pairs.tolist():
+        a, b = divmod(key, n)
+        adj[a].append(b)
+        adj[b].append(a)
+    deg = [len(x) for x in adj]
+    heap = [(d, v) for v, d in enumerate(deg)]
+    heapq.heapify(heap)
+    gone = [False] * n
+    core = np.zeros(n, dtype=np.int64)
+    k = 0
+    while heap:
+        d, v = heapq.heappop(heap)
+        if gone[v] or d != deg[v]:
+            continue
+        gone[v] = True
+        k = max(k, d)
+        core[v] = k
+        for u in adj[v]:
+            if not gone[u]:
+                deg[u] -= 1
+                heapq.heappush(heap, (deg[u], u))
+    return core
+
+
+def core_order_levels(n: int, edges: np.ndarray) -> np.ndarray:
+    """Ranks of the level-synchronous core ordering (the reading of the core
+    ordering of Sec. 1.3 taken by the device path), computed one vertex at a
+    time: at level k, every remaining vertex of degree <= k is removed in one
+    round; the vertices whose degree falls to k while that round's vertices
+    are deleted form the next round; when a round is empty, k moves up to the
+    smallest remaining degree (or k+1).  Vertices are ranked by (round, id).
+    The outcome does not depend on the order in which a round's deletions are
+    made: a vertex enters the next round when its degree reaches k, whichever
+    neighbour brings it there."""
+    e = np.asarray(edges, dtype=np.int64).reshape(-1, 2)
+    e = e[e[:, 0] != e[:, 1]]
+    lo, hi = np.minimum(e[:, 0], e[:, 1]), np.maximum(e[:, 0], e[:, 1])
+    adj = [[] for _ in range(n)]
+    for key in np.unique(lo * n + hi).tolist():
+        a, b = divmod(key, n)
+        adj[a].append(b)
+        adj[b].append(a)
+    deg = [len(x) for x in adj]
+    removed = [False] * n
+    rnd_of = [0] * n
+    active = set(range(n))
+    k, rnd = 0, 0
+    while active:
+        frontier = sorted(v for v in active if deg[v] <= k)
+        if not frontier:
+            k = max(k + 1, min(deg[v] for v in active))
+            continue
+        for v in frontier:
+            removed[v] = True
+        active.difference_update(frontier)
+        while frontier:
+            nxt = []
+            for v in frontier:
+                rnd_of[v] = rnd
+                for u in adj[v]:
+                    if not removed[u]:
+                        deg[u] -= 1
+                        if deg[u] == k:
+                            removed[u] = True
+                            nxt.append(u)
+            active.difference_update(nxt)
+            rnd += 1
+            frontier = nxt
+        k += 1
+    order = sorted(range(n), key=lambda v: (rnd_of[v], v))
+    rank = np.empty(n, dtype=np.uint32)
+    rank[np.asarray(order, dtype=np.int64)] = np.arange(n, dtype=np.uint32)
+    return rank

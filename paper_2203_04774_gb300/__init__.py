@@ -216,7 +216,7 @@ def tl_order_apply(g, rank) -> None:
     _check(lib().tl_order_apply(g, ptr, on_dev), "tl_order_apply")
 
 
-TL_ORDER_DEGREE, TL_ORDER_SPLIT = 0, 1
+TL_ORDER_DEGREE, TL_ORDER_SPLIT, TL_ORDER_CORE = 0, 1, 2
 
 
 def tl_order_compute(g, kind: int, rank=None):
@@ -417,7 +417,7 @@ class Graph:
         return cls._wrap(tl_graph_union([g.h for g in graphs], ranks, stream))
 
     def order_compute(self, kind: int, rank=None):
-        """Device ordering (TL_ORDER_DEGREE / TL_ORDER_SPLIT) as ranks; a new
+        """Device ordering (TL_ORDER_DEGREE / _SPLIT / _CORE) as ranks; a new
         CUDA int32 tensor unless ``rank`` is given."""
         if rank is None:
             import torch

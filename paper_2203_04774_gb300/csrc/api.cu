@@ -452,8 +452,8 @@ tl_status tl_order_apply(tl_graph *G, const uint32_t *rank, int rank_on_device) 
 tl_status tl_order_compute(tl_graph *G, tl_order_kind kind, uint32_t *rank, int rank_on_device) {
   TL_API_BEGIN
   if (!G || !rank) tl::fail(TL_EINVAL, "graph or rank is NULL");
-  if (kind != TL_ORDER_DEGREE && kind != TL_ORDER_SPLIT)
-    tl::fail(TL_EINVAL, "kind must be TL_ORDER_DEGREE or TL_ORDER_SPLIT");
+  if (kind != TL_ORDER_DEGREE && kind != TL_ORDER_SPLIT && kind != TL_ORDER_CORE)
+    tl::fail(TL_EINVAL, "kind must be TL_ORDER_DEGREE, TL_ORDER_SPLIT or TL_ORDER_CORE");
   tl::compute_order(G->g, kind, rank, rank_on_device != 0);
   TL_API_END
 }

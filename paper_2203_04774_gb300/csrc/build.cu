@@ -287,6 +287,31 @@ void finish_edge_set(DeviceGraph &g, uint64_t m_in) {
   g.sort_tmp.release();
 }
 
+void csr_halves(const uint64_t *E, uint64_t m, uint32_t n, uint64_t *off_a, uint32_t *adj_a,
+                uint64_t *off_b, uint32_t *adj_b, DevBuf &ka, DevBuf &kb, DevBuf &tmp,
+                DevBuf &scan, cudaStream_t s) {
+  if (m == 0) {
+    TL_CUDA(cudaMemsetAsync(off_a, 0, ((uint64_t)n + 1) * 8, s));
+    TL_CUDA(cudaMemsetAsync(off_b, 0, ((uint64_t)n + 1) * 8, s));
+    return;
+  }
+  k_offsets<<<grid_for((uint64_t)n + 1, kThreads), kThreads, 0, s>>>(E, m, n, off_a);
+  TL_CHECK_LAUNCH();
+  k_low_half<<<grid_for(m, kThreads), kThreads, 0, s>>>(E, m, adj_a);
+  TL_CHECK_LAUNCH();
+  ka.reserve(m * 8);
+  kb.reserve(m * 8);
+  k_swap_halves<<<grid_for(m, kThreads), kThreads, 0, s>>>(E, m, ka.as<uint64_t>());
+  TL_CHECK_LAUNCH();
+  const int b = bits_for(n > 1 ? n - 1 : 1);
+  radix_sort_u64(ka.as<uint64_t>(), kb.as<uint64_t>(), m, 0, 0, 32, b, tmp, scan, s);
+  k_offsets<<<grid_for((uint64_t)n + 1, kThreads), kThreads, 0, s>>>(ka.as<uint64_t>(), m, n,
+                                                                    off_b);
+  TL_CHECK_LAUNCH();
+  k_low_half<<<grid_for(m, kThreads), kThreads, 0, s>>>(ka.as<uint64_t>(), m, adj_b);
+  TL_CHECK_LAUNCH();
+}
+
 bool is_permutation(const uint32_t *rank, uint32_t n, uint32_t *flag, cudaStream_t s) {
   DevBuf cnt(s);
   cnt.reserve((uint64_t)n * 4);
@@ -391,19 +416,26 @@ void compute_order(DeviceGraph &g, int kind, uint32_t *rank, bool on_device) {
   deg.reserve((uint64_t)n * 4);
   ka.reserve((uint64_t)n * 8);
   kb.reserve((uint64_t)n * 8);
-  TL_CUDA(cudaMemsetAsync(deg.p, 0, (uint64_t)n * 4, s));
-  if (g.m) {
-    k_degrees<<<grid_for(g.m, kThreads), kThreads, 0, s>>>(g.E.as<uint64_t>(), g.m,
-                                                           deg.as<uint32_t>());
-    TL_CHECK_LAUNCH();
-  }
-  const int bits = bits_for(n);  // degrees are < n < 2^bits
-  const uint32_t top = (uint32_t)((1ull << bits) - 1);
   const int split = kind == TL_ORDER_SPLIT;
-  k_degree_keys<<<grid_for(n, kThreads), kThreads, 0, s>>>(deg.as<uint32_t>(), n, split, top,
-                                                           ka.as<uint64_t>());
-  TL_CHECK_LAUNCH();
-  radix_sort_u64(ka.as<uint64_t>(), kb.as<uint64_t>(), n, 0, 0, 32, bits, tmp, scan, s);
+  if (kind == TL_ORDER_CORE) {
+    // keys (round << 32 | v) of the level-synchronous peeling (core.cu)
+    const uint32_t rounds = core_peel_keys(g, ka.as<uint64_t>());
+    radix_sort_u64(ka.as<uint64_t>(), kb.as<uint64_t>(), n, 0, 0, 32, bits_for(rounds), tmp,
+                   scan, s);
+  } else {
+    TL_CUDA(cudaMemsetAsync(deg.p, 0, (uint64_t)n * 4, s));
+    if (g.m) {
+      k_degrees<<<grid_for(g.m, kThreads), kThreads, 0, s>>>(g.E.as<uint64_t>(), g.m,
+                                                             deg.as<uint32_t>());
+      TL_CHECK_LAUNCH();
+    }
+    const int bits = bits_for(n);  // degrees are < n < 2^bits
+    const uint32_t top = (uint32_t)((1ull << bits) - 1);
+    k_degree_keys<<<grid_for(n, kThreads), kThreads, 0, s>>>(deg.as<uint32_t>(), n, split, top,
+                                                             ka.as<uint64_t>());
+    TL_CHECK_LAUNCH();
+    radix_sort_u64(ka.as<uint64_t>(), kb.as<uint64_t>(), n, 0, 0, 32, bits, tmp, scan, s);
+  }
   uint32_t *dst = rank;
   if (!on_device) {
     out.reserve((uint64_t)n * 4);

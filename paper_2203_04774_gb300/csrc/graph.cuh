@@ -48,13 +48,21 @@ void build_edge_set_parts(DeviceGraph &g, uint32_t k, const uint32_t *n, const u
 //   current ordering (identity when none was applied); builds the union's DAG.
 void build_union(DeviceGraph &u, uint32_t k, const DeviceGraph *const *parts,
                  const uint32_t *const *rank);
+// N+ / N- halves of the CSR of keys sorted by (high, low) half: off_a/adj_a by
+// high half, off_b/adj_b by low half (rows ascending); ka, kb: m-key scratch.
+void csr_halves(const uint64_t *E, uint64_t m, uint32_t n, uint64_t *off_a, uint32_t *adj_a,
+                uint64_t *off_b, uint32_t *adj_b, DevBuf &ka, DevBuf &kb, DevBuf &tmp,
+                DevBuf &scan, cudaStream_t s);
+// Level-synchronous core peeling (core.cu): keys[v] = round << 32 | v; returns
+// the number of rounds.
+uint32_t core_peel_keys(DeviceGraph &g, uint64_t *keys);
 // True iff rank[0..n) (device) is a permutation of [0, n); `flag` is one
 // device uint32 of scratch.  Synchronises s.
 bool is_permutation(const uint32_t *rank, uint32_t n, uint32_t *flag, cudaStream_t s);
 // a2-a5: validate the permutation, relabel, orient, CSR out/in, cost.
 // rank == nullptr applies the identity ordering.
 void build_dag(DeviceGraph &g, const uint32_t *rank, bool on_device);
-// Degree (kind 0) or Split (kind 1) ordering of the loaded graph into rank[n];
+// Degree (kind 0), Split (kind 1) or core (kind 2) ordering of the loaded graph into rank[n];
 // on a union, part by part (part i's ranks are vbase[i] + its own ranks).
 void compute_order(DeviceGraph &g, int kind, uint32_t *rank, bool on_device);
 

@@ -125,14 +125,15 @@ def test_load_parts_identity_and_degree_orderings():
         _check_union(u, parts, ident, [alg] * len(parts))
     # device orderings of a union are computed part by part
     vb = _vbase(sizes)
-    for kind, host in ((tl.TL_ORDER_DEGREE, synth.order_degree),
-                       (tl.TL_ORDER_SPLIT, synth.order_split)):
+    for kind, host in ((tl.TL_ORDER_DEGREE, lambda n, e, off: synth.order_degree(off)),
+                       (tl.TL_ORDER_SPLIT, lambda n, e, off: synth.order_split(off)),
+                       (tl.TL_ORDER_CORE, lambda n, e, off: oracle.core_order_levels(n, e))):
         rank_u = u.order_compute(kind).cpu().numpy().astype(np.int64)
         local = []
         for i, (n, e) in enumerate(parts):
             off, _ = synth.simple_csr(n, e)
             r = rank_u[vb[i]:vb[i + 1]] - vb[i]
-            assert np.array_equal(r, host(off)), (kind, i)
+            assert np.array_equal(r, host(n, e, off)), (kind, i)
             local.append(r.astype(np.uint32))
         u.order_apply(_dev(rank_u.astype(np.uint32)))
         _check_union(u, parts, local, [tl.TL_APP] * 5 + [tl.TL_APM] * 5)

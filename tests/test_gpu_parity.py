@@ -336,6 +336,42 @@ def test_device_orderings_match_host(kind):
         g.free()
 
 
+def test_device_core_ordering_matches_oracle():
+    """TL_ORDER_CORE is the level-synchronous core ordering, rank for rank
+    (oracle.core_order_levels); it is a degeneracy ordering (coreness
+    non-decreasing, d+_v <= c_v) and lists the same triangles."""
+    k = 3000
+    spokes = np.stack([np.zeros(k, np.uint32), np.arange(1, k + 1, dtype=np.uint32)], 1)
+    rim = np.stack([np.arange(1, k + 1, dtype=np.uint32),
+                    np.r_[np.arange(2, k + 1), 1].astype(np.uint32)], 1)
+    cases = [(7, synth.fig3_graph()), (3000, synth.chung_lu(3000, 12, 2.3, 8)),
+             (20000, synth.chung_lu(20000, 30, 2.1, 9)), (40, synth.complete(40)),
+             (4000, synth.star(4000, 11)), (1, np.zeros((0, 2), np.uint32)),
+             (50, np.zeros((0, 2), np.uint32)), (k + 1, np.concatenate([spokes, rim])),
+             (5000, synth.complete_bipartite(10, 4990))]
+    for n, e in cases:
+        want = oracle.core_order_levels(n, e)
+        g = tl.Graph(n, _dev(e))
+        got = g.order_compute(tl.TL_ORDER_CORE).cpu().numpy().view(np.uint32)
+        assert np.array_equal(got, want), n
+        c = oracle.core_numbers(n, e)
+        assert np.all(np.diff(c[np.argsort(got)]) >= 0)
+        off, adj = synth.simple_csr(n, e)
+        src = np.repeat(np.arange(n), np.diff(off.astype(np.int64)))
+        r = got.astype(np.int64)
+        dplus = np.bincount(src[r[adj.astype(np.int64)] > r[src]], minlength=n)
+        assert np.all(dplus <= c)
+        g.order_apply(_dev(got))
+        ref = oracle.Graph(n, e)
+        ref.order_apply(want)
+        for alg in (tl.TL_APP, tl.TL_APM):
+            assert g.cost(alg) == ref.cost(alg)
+            nt, _, h, _ = g.list_count_hash(alg)
+            _, rc, rh, _ = ref.list(alg, store=False)
+            assert (nt, h) == (rc, rh)
+        g.free()
+
+
 def test_device_generator_on_gpu_matches_host():
     from paper_2203_04774_gb300.synth import device as dev
     e = synth.chung_lu(50000, 20, 2.2, 4)

@@ -351,3 +351,74 @@ def test_set_hash_is_order_free_and_sensitive():
     # all 4060 per-triple values distinct
     per = [oracle.hash_triples(t[i:i + 1]) for i in range(len(t))]
     assert len(set(per)) == len(per)
+
+
+def test_core_numbers_closed_forms_and_brute_force():
+    """Coreness (Sec. 1.3): K_n -> n-1, trees and stars -> 1, a cycle -> 2,
+    isolated vertices -> 0; K_5 joined to a path -> 4 on the clique, 1 on the
+    path; and on small random graphs, the definition checked by brute force
+    (c_v = the largest k whose k-core, found by deleting vertices of degree
+    < k until none is left, contains v)."""
+    assert list(oracle.core_numbers(6, synth.complete(6))) == [5] * 6
+    assert list(oracle.core_numbers(20, synth.random_tree(20, 3))) == [1] * 20
+    assert list(oracle.core_numbers(9, synth.star(9))) == [1] * 9
+    cyc = np.stack([np.arange(7), (np.arange(7) + 1) % 7], 1)
+    assert list(oracle.core_numbers(7, cyc)) == [2] * 7
+    assert list(oracle.core_numbers(4, np.zeros((0, 2), np.uint32))) == [0] * 4
+    path = np.array([[4, 5], [5, 6], [6, 7]])
+    c = oracle.core_numbers(8, np.concatenate([synth.complete(5), path]))
+    assert list(c) == [4] * 5 + [1] * 3
+
+    def brute(n, e):
+        nb = [set() for _ in range(n)]
+        for a, b in e:
+            if a != b:
+                nb[a].add(b)
+                nb[b].add(a)
+        core = [0] * n
+        for k in range(1, n):
+            alive = set(range(n))
+            changed = True
+            while changed:
+                changed = False
+                for v in list(alive):
+                    if len(nb[v] & alive) < k:
+                        alive.discard(v)
+                        changed = True
+            for v in alive:
+                core[v] = k
+        return core
+
+    for seed in range(6):
+        e = synth.gnp(25, 0.25, 40 + seed)
+        assert list(oracle.core_numbers(25, e)) == brute(25, e.tolist()), seed
+
+
+def test_core_order_levels_is_a_degeneracy_ordering():
+    """The level-synchronous core ordering: a permutation along which the
+    coreness never decreases and every vertex has at most c_v later
+    neighbours (d+_v <= c_v); its maximum d+ is the degeneracy max_v c_v.
+    Worked cases: on K_5 plus a pendant path the path goes first (level 1)
+    and the clique last; on a star the leaves are taken in one round before
+    the hub's degree falls, so the hub comes last."""
+    cases = [(8, np.concatenate([synth.complete(5), np.array([[4, 5], [5, 6], [6, 7]])])),
+             (9, synth.star(9))]
+    for seed in range(8):
+        n = 60 + 20 * seed
+        cases.append((n, synth.chung_lu(n, 8, 2.3, 70 + seed)))
+    for n, e in cases:
+        r = oracle.core_order_levels(n, e).astype(np.int64)
+        assert sorted(r.tolist()) == list(range(n))
+        c = oracle.core_numbers(n, e)
+        inv = np.argsort(r)
+        assert np.all(np.diff(c[inv]) >= 0)
+        off, adj = synth.simple_csr(n, e)
+        src = np.repeat(np.arange(n), np.diff(off.astype(np.int64)))
+        later = r[adj.astype(np.int64)] > r[src]
+        dplus = np.bincount(src[later], minlength=n)
+        assert np.all(dplus <= c)
+        assert dplus.max(initial=0) == c.max(initial=0)
+    r = oracle.core_order_levels(8, cases[0][1])
+    assert sorted(r[5:].tolist()) == [0, 1, 2] and sorted(r[:5].tolist()) == [3, 4, 5, 6, 7]
+    r = oracle.core_order_levels(9, synth.star(9))
+    assert r[0] == 8
