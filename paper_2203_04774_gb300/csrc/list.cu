@@ -103,6 +103,38 @@ __device__ __forceinline__ bool hash_find(const uint32_t *H, int lg, uint32_t z)
   }
 }
 
+// Bucketed table for the CTA tiers: 2^lgb buckets of four slots, key r in
+// bucket bslot(r) or, when that is full, the next ones (linear probing by
+// bucket).  A thread writes slot s of a bucket only after finding slots
+// 0..s-1 taken, so the taken slots of a bucket are always a prefix: a bucket
+// whose last slot is empty ends a search.  A lookup reads one bucket with a
+// single 16-byte shared-memory load.
+__device__ __forceinline__ uint32_t bslot(uint32_t r, int lgb) {
+  return (r * 0x9E3779B1u) >> (32 - lgb);
+}
+
+__device__ __forceinline__ void bucket_insert(uint32_t *H, int lgb, uint32_t r) {
+  const uint32_t mask = (1u << lgb) - 1u;
+  uint32_t b = bslot(r, lgb);
+  for (;;) {
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+      if (atomicCAS(&H[4 * b + s], kEmpty, r) == kEmpty) return;
+    b = (b + 1) & mask;
+  }
+}
+
+__device__ __forceinline__ bool bucket_find(const uint32_t *H, int lgb, uint32_t z) {
+  const uint32_t mask = (1u << lgb) - 1u;
+  uint32_t b = bslot(z, lgb);
+  for (;;) {
+    const uint4 q = reinterpret_cast<const uint4 *>(H)[b];
+    if (q.x == z || q.y == z || q.z == z || q.w == z) return true;
+    if (q.w == kEmpty) return false;
+    b = (b + 1) & mask;
+  }
+}
+
 // Filter bit of rank r (2^20 bits) for the hub tier's shared-memory filter.
 __device__ __forceinline__ uint32_t fslot(uint32_t r) { return (r * 0x85EBCA77u) >> 12; }
 
@@ -456,7 +488,7 @@ __global__ void __launch_bounds__(THREADS, TIER == 3 ? 1 : 4) k_list_cta(ListArg
         if (use_bitmap) {
           s_mode = 0;
         } else {
-          // mid tier: load <= 1/4, so most lookups end at the first slot
+          // mid tier: load <= 1/4, so most lookups end at the first bucket
           const uint32_t max_slots = TIER == 2 ? (uint32_t)kMidSlots : kHashMaxSlots;
           const uint64_t want = TIER == 2 ? 4 * p : 2 * p;
           uint32_t lg = 6;
@@ -486,10 +518,11 @@ __global__ void __launch_bounds__(THREADS, TIER == 3 ? 1 : 4) k_list_cta(ListArg
         const uint32_t r = a.padj[q];
         atomicOr(&sm[r >> 5], 1u << (r & 31));
       }
-    } else if (mode == 1) {
+    } else if (mode == 1) {  // lg = log2(slots); buckets of four
       for (uint32_t i = threadIdx.x; i < (1u << lg); i += THREADS) sm[i] = kEmpty;
       __syncthreads();
-      for (uint64_t q = pb + threadIdx.x; q < pe; q += THREADS) hash_insert(sm, lg, a.padj[q]);
+      for (uint64_t q = pb + threadIdx.x; q < pe; q += THREADS)
+        bucket_insert(sm, lg - 2, a.padj[q]);
     } else if (mode == 3) {
       uint32_t *gh = a.ghash + (uint64_t)blockIdx.x * kGHashSlots;
       for (uint32_t i = threadIdx.x; i < kFilterWords; i += THREADS) sm[i] = 0;
@@ -519,8 +552,8 @@ __global__ void __launch_bounds__(THREADS, TIER == 3 ? 1 : 4) k_list_cta(ListArg
                         &s_cnt, unused, probes);
     } else if (mode == 1) {
       scan_items<false>(a, pb, pe, ~0ull, wa, wb, inv_x,
-                        [&](uint32_t z) { return hash_find(sm, lg, z); }, slab, &s_cnt, unused,
-                        probes);
+                        [&](uint32_t z) { return bucket_find(sm, lg - 2, z); }, slab, &s_cnt,
+                        unused, probes);
     } else if (mode == 3) {
       const uint32_t *gh = a.ghash + (uint64_t)blockIdx.x * kGHashSlots;
       scan_items<false>(a, pb, pe, ~0ull, wa, wb, inv_x,
