@@ -1,4 +1,5 @@
 // C ABI of libtl (declared in include/tl.h).
+#include <algorithm>
 #include <atomic>
 #include <cstring>
 #include <mutex>
@@ -56,7 +57,8 @@ struct PinnedCtl {
 struct tl_graph {
   tl::DeviceGraph g;
   // listing workspace
-  tl::DevBuf wseed, WP, ctl, chunks, slabs, retry, ghash;
+  tl::DevBuf wseed, WP, ctl, chunks, slabs, retry, rretry, ghash;
+  uint64_t rretry_cap = 0;  // RetryRange records per half of rretry
   // per-vertex classification (tiers 0, 1: weights and flags; tiers 2, 3: pieces),
   // their prefixes, and the compacted vertex lists of tiers 0 and 1
   tl::DevBuf tw[2], tf[2], tpref[2], tpos[2], tx[2], twp[2], tstart[2], pieces[2],
@@ -70,7 +72,8 @@ struct tl_graph {
   uint64_t tier_count[2] = {0, 0};
   void bind(cudaStream_t s) {
     g.bind(s);
-    for (tl::DevBuf *b : {&wseed, &WP, &ctl, &chunks, &slabs, &retry, &ghash}) b->stream = s;
+    for (tl::DevBuf *b : {&wseed, &WP, &ctl, &chunks, &slabs, &retry, &rretry, &ghash})
+      b->stream = s;
     for (int t = 0; t < 2; ++t)
       for (tl::DevBuf *b : {&tw[t], &tf[t], &tpref[t], &tpos[t], &tx[t], &twp[t], &tstart[t],
                             &pieces[t], &piece_prefix[t], &task_x[t]})
@@ -213,10 +216,8 @@ tl_status list_impl(tl_graph *G, int alg, uint32_t xb, uint32_t xe, size_t chunk
   bucketize(G, alg, xb, xe);
 
   uint64_t slab_words = 0, max_tasks = 1;
-  for (int t = 0; t < tl::kTiers; ++t) {
-    // warp tiers: one slab per warp; mid and large tiers: one per CTA
-    const uint64_t w =
-        (uint64_t)tl::tier_grid(t) * (t < 2 ? (tl::kWarpThreads / 32) : 1) * tl::slab_cap(t);
+  for (int t = 0; t < 2; ++t) {  // warp tiers: one global slab per warp
+    const uint64_t w = (uint64_t)tl::tier_grid(t) * (tl::kWarpThreads / 32) * tl::slab_cap(t);
     slab_words = w > slab_words ? w : slab_words;
     max_tasks = G->n_tasks[t] > max_tasks ? G->n_tasks[t] : max_tasks;
   }
@@ -232,6 +233,23 @@ tl_status list_impl(tl_graph *G, int alg, uint32_t xb, uint32_t xe, size_t chunk
   tl::ListCtl *hc = G->pctl->h;
   uint32_t *chunk[2] = {G->chunks.as<uint32_t>(), G->chunks.as<uint32_t>() + 3 * cap};
   uint32_t *retry[2] = {G->retry.as<uint32_t>(), G->retry.as<uint32_t>() + max_tasks};
+  // CTA tiers: each launch queues at most one range per resident warp, plus
+  // the ranges it did not fetch
+  const uint64_t warps_cta = std::max<uint64_t>((uint64_t)tl::tier_grid(2) * (tl::kMidThreads / 32),
+                                                (uint64_t)tl::tier_grid(3) * (tl::kLargeThreads / 32));
+  auto rr_half = [&](int h) { return G->rretry.as<tl::RetryRange>() + h * G->rretry_cap; };
+  auto reserve_ranges = [&](int in_half, uint64_t n_in, uint64_t need) {
+    if (need <= G->rretry_cap) return;
+    const uint64_t cap2 = std::max<uint64_t>(need, 2 * G->rretry_cap);
+    tl::DevBuf nb(s);
+    nb.reserve(2 * cap2 * sizeof(tl::RetryRange));
+    if (n_in)
+      TL_CUDA(cudaMemcpyAsync(nb.as<tl::RetryRange>() + in_half * cap2, rr_half(in_half),
+                              n_in * sizeof(tl::RetryRange), cudaMemcpyDeviceToDevice, s));
+    std::swap(G->rretry.p, nb.p);
+    std::swap(G->rretry.bytes, nb.bytes);
+    G->rretry_cap = cap2;
+  };
 
   tl::ListArgs a{};
   a.n = g.n;
@@ -278,12 +296,18 @@ tl_status list_impl(tl_graph *G, int alg, uint32_t xb, uint32_t xe, size_t chunk
     if (launch) {
       std::memset(hc, 0, sizeof(*hc));
       hc->cursor = filled;
-      hc->valid_end = filled;
+      hc->first_fail = ~0ull;
       TL_CUDA(cudaMemcpyAsync(a.ctl, hc, sizeof(*hc), cudaMemcpyHostToDevice, s));
       a.chunk = chunk[cur];
-      a.retry_in = retry[rsel];
       a.n_retry = P->n_retry;
-      a.retry_out = retry[rsel ^ 1];
+      if (P->kind < 2) {
+        a.retry_in = retry[rsel];
+        a.retry_out = retry[rsel ^ 1];
+      } else {
+        reserve_ranges(rsel, P->n_retry, P->n_retry + warps_cta);
+        a.rr_in = rr_half(rsel);
+        a.rr_out = rr_half(rsel ^ 1);
+      }
       a.fresh_base = P->fresh;
       a.n_tasks = P->n_tasks;
       a.slab_cap = tl::slab_cap(P->kind);
@@ -315,9 +339,13 @@ tl_status list_impl(tl_graph *G, int alg, uint32_t xb, uint32_t xe, size_t chunk
       TL_CUDA(cudaEventElapsedTime(&ms, G->ev[0], G->ev[1]));
       st.kernel_ms[P->kind] += ms;
     }
-    total_tri += hc->triangles;
+    // the reservations that fit are the chunk prefix [filled, valid_end)
+    const uint64_t valid_end = hc->overflow ? std::min<uint64_t>(hc->first_fail, hc->cursor)
+                                            : hc->cursor;
+    const uint64_t launch_tri = valid_end - filled;
+    total_tri += launch_tri;
     total_probes += hc->probes;
-    st.kernel_triangles[P->kind] += hc->triangles;
+    st.kernel_triangles[P->kind] += launch_tri;
     st.kernel_probes[P->kind] += hc->probes;
     const uint32_t fetched = hc->fetch;
     const uint32_t used_retry = fetched < P->n_retry ? fetched : P->n_retry;
@@ -325,18 +353,22 @@ tl_status list_impl(tl_graph *G, int alg, uint32_t xb, uint32_t xe, size_t chunk
     if (fresh_fetched > P->n_tasks - P->fresh) fresh_fetched = P->n_tasks - P->fresh;
     uint32_t nr_out = hc->n_retry_out;
     if (used_retry < P->n_retry) {  // retry entries nobody fetched carry over
-      TL_CUDA(cudaMemcpyAsync(retry[rsel ^ 1] + nr_out, retry[rsel] + used_retry,
-                              (size_t)(P->n_retry - used_retry) * 4, cudaMemcpyDeviceToDevice,
-                              s));
-      nr_out += P->n_retry - used_retry;
+      const uint64_t left = P->n_retry - used_retry;
+      if (P->kind < 2) {
+        TL_CUDA(cudaMemcpyAsync(retry[rsel ^ 1] + nr_out, retry[rsel] + used_retry, left * 4,
+                                cudaMemcpyDeviceToDevice, s));
+      } else {
+        TL_CUDA(cudaMemcpyAsync(rr_half(rsel ^ 1) + nr_out, rr_half(rsel) + used_retry,
+                                left * sizeof(tl::RetryRange), cudaMemcpyDeviceToDevice, s));
+      }
+      nr_out += (uint32_t)left;
     }
-    const bool progress = hc->valid_end > filled || fresh_fetched > 0 ||
-                          nr_out < P->n_retry + fresh_fetched || hc->triangles > 0 ||
-                          hc->probes > 0;
+    const bool progress = valid_end > filled || fresh_fetched > 0 ||
+                          nr_out < P->n_retry + fresh_fetched || hc->probes > 0;
     P->fresh += fresh_fetched;
     P->n_retry = nr_out;
     rsel ^= 1;
-    filled = hc->valid_end;
+    filled = valid_end;
     if (hc->overflow) {
       if (filled == 0 && !progress) tl::fail(TL_ECUDA, "listing made no progress");
       pending = cur;

@@ -161,12 +161,12 @@ __device__ __forceinline__ int64_t fetch_task(ListCtl *ctl, const ListArgs &a) {
   return (t < a.n_tasks) ? (int64_t)t : -1;
 }
 
-// Copy a task's slab to the chunk: each slab entry is (original id of x,
+// Copy a warp-tier task's slab to the chunk: each entry is (original id of x,
 // original id of y, rank of z); z is translated and the triple sorted here,
-// where all gathers of the task are independent.
-__device__ __forceinline__ void copy_out(const ListArgs &a, const uint32_t *slab, uint32_t cnt,
-                                         uint32_t *dst, uint32_t tid, uint32_t nthreads) {
-  // four triples per thread per round, their loads and gathers issued together
+// four triples per thread per round with their gathers issued together.
+__device__ __forceinline__ void copy_out(const uint32_t *__restrict__ inv, const uint32_t *slab,
+                                         uint32_t cnt, uint32_t *dst, uint32_t tid,
+                                         uint32_t nthreads) {
   for (uint32_t i0 = tid; i0 < cnt; i0 += 4 * nthreads) {
     uint32_t t[4][3];
 #pragma unroll
@@ -180,7 +180,7 @@ __device__ __forceinline__ void copy_out(const ListArgs &a, const uint32_t *slab
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u)
-      if (i0 + u * nthreads < cnt) t[u][2] = a.inv[t[u][2]];
+      if (i0 + u * nthreads < cnt) t[u][2] = __ldg(inv + t[u][2]);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const uint32_t i = i0 + u * nthreads;
@@ -196,37 +196,105 @@ __device__ __forceinline__ void copy_out(const ListArgs &a, const uint32_t *slab
   }
 }
 
-// End of a task: reserve chunk room for the slab, copy it, or queue the task.
-__device__ void commit_task(ListCtl *ctl, const ListArgs &a, int64_t t, const uint32_t *slab,
-                            uint32_t cnt, unsigned long long probes, uint32_t *s_ok,
-                            unsigned long long *s_pos) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t ok = 1;
-    unsigned long long pos = 0;
-    if (cnt > 0) {
-      pos = atomicAdd(&ctl->cursor, (unsigned long long)cnt);
-      if (pos + cnt > a.chunk_cap) ok = 0;
-    }
-    if (ok) {
-      if (cnt > 0) {
-        atomicMax(&ctl->valid_end, pos + cnt);
-        atomicAdd(&ctl->triangles, (unsigned long long)cnt);
-      }
-      atomicAdd(&ctl->probes, probes);
-    } else {
+// Output state of one warp of a CTA tier (see kWarpBuf).
+struct WarpOut {
+  uint32_t *buf;                   // shared memory: kWarpBuf (original id of y, rank of z)
+  uint32_t cnt;                    // entries in buf (the same in every lane)
+  uint64_t safe;                   // the warp's tests before `safe` are committed
+  unsigned long long probes_safe;  // this lane's tests before `safe`
+  bool failed;                     // a reservation did not fit: the warp stopped
+};
+
+// Copy a warp's buffer of cnt > 0 entries (original id of y, rank of z) to
+// the chunk as sorted original-id triples with x, after reserving room with
+// one atomic; four gathers of z per lane are issued together.  Returns false
+// if the chunk is full.  Scalar arguments only, so that the caller's state
+// stays in registers around the call.
+__device__ __noinline__ bool warp_flush(ListCtl *ctl, uint32_t *chunk, uint64_t chunk_cap,
+                                        const uint32_t *__restrict__ inv, const uint32_t *buf,
+                                        uint32_t cnt, uint32_t inv_x) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long pos = 0;
+  uint32_t ok = 1;
+  if (lane == 0) {
+    // once one reservation has failed every later one fails too (the cursor
+    // only grows), so the result of the add alone decides
+    pos = atomicAdd(&ctl->cursor, (unsigned long long)cnt);
+    if (pos + cnt > chunk_cap) {
+      ok = 0;
+      atomicMin(&ctl->first_fail, pos);
       atomicExch(&ctl->overflow, 1u);
-      uint32_t r = atomicAdd(&ctl->n_retry_out, 1u);
-      a.retry_out[r] = (uint32_t)t;
     }
-    *s_ok = ok;
-    *s_pos = pos;
   }
-  __syncthreads();
-  if (*s_ok && cnt > 0) {
-    copy_out(a, slab, cnt, a.chunk + 3ull * (*s_pos), threadIdx.x, blockDim.x);
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  if (!ok) return false;
+  pos = (unsigned long long)__shfl_sync(0xffffffffu, (long long)pos, 0);
+  uint32_t *dst = chunk + 3ull * pos;
+  const uint2 *b2 = reinterpret_cast<const uint2 *>(buf);
+  for (uint32_t i0 = lane; i0 < cnt; i0 += 128) {
+    uint2 e[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (i0 + 32 * u < cnt) e[u] = b2[i0 + 32 * u];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (i0 + 32 * u < cnt) e[u].y = __ldg(inv + e[u].y);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const uint32_t i = i0 + 32 * u;
+      if (i < cnt) {
+        uint32_t p = inv_x, q = e[u].x, r = e[u].y;
+        sort3(p, q, r);
+        __stcs(dst + 3 * i, p);
+        __stcs(dst + 3 * i + 1, q);
+        __stcs(dst + 3 * i + 2, r);
+      }
+    }
   }
-  __syncthreads();
+  __syncwarp();
+  return true;
+}
+
+// Commit a warp's buffer: afterwards every test before `cur` is committed.
+// On a full chunk sets o.failed and leaves o.safe where it was.
+__device__ __forceinline__ bool warp_commit(const ListArgs &a, WarpOut &o, uint32_t inv_x,
+                                            uint64_t cur, unsigned long long probes) {
+  if (o.cnt > 0) {
+    if (!warp_flush(a.ctl, a.chunk, a.chunk_cap, a.inv, o.buf, o.cnt, inv_x)) {
+      o.failed = true;
+      return false;
+    }
+    o.cnt = 0;
+  }
+  o.safe = cur;
+  o.probes_safe = probes;
+  return true;
+}
+
+// Next piece of work of a CTA tier (thread 0): a retry range, else the next
+// fresh task's piece [ia, ib) of B vertex x.  False when the chunk is full or
+// no work is left.
+__device__ __forceinline__ bool fetch_range(const ListArgs &a, uint32_t &x, uint64_t &ia,
+                                            uint64_t &ib) {
+  if (*(volatile uint32_t *)&a.ctl->overflow) return false;
+  const uint32_t idx = atomicAdd(&a.ctl->fetch, 1u);
+  if (idx < a.n_retry) {
+    const RetryRange r = a.rr_in[idx];
+    x = r.x;
+    ia = r.i0;
+    ib = r.i1;
+    return true;
+  }
+  const uint64_t t = a.fresh_base + (idx - a.n_retry);
+  if (t >= a.n_tasks) return false;
+  x = a.task_x[t];
+  const uint64_t piece = t - a.piece_prefix[x - a.x_begin];
+  const uint64_t pb = a.poff[x], pe = a.poff[x + 1];
+  const uint64_t w1 = a.WP[pe];
+  const uint64_t pw = piece_work(a.tier, pe - pb);
+  ia = a.WP[pb] + piece * pw;
+  ib = ia + pw < w1 ? ia + pw : w1;
+  return true;
 }
 
 // Warp-level end of a warp-tier task: reserve chunk room for the warp's slab
@@ -242,12 +310,9 @@ __device__ void commit_warp(ListCtl *ctl, const ListArgs &a, int64_t t, const ui
       if (pos + cnt > a.chunk_cap) ok = 0;
     }
     if (ok) {
-      if (cnt > 0) {
-        atomicMax(&ctl->valid_end, pos + cnt);
-        atomicAdd(&ctl->triangles, (unsigned long long)cnt);
-      }
       atomicAdd(&ctl->probes, probes);
     } else {
+      atomicMin(&ctl->first_fail, pos);
       atomicExch(&ctl->overflow, 1u);
       const uint32_t r = atomicAdd(&ctl->n_retry_out, 1u);
       a.retry_out[r] = (uint32_t)t;
@@ -256,20 +321,23 @@ __device__ void commit_warp(ListCtl *ctl, const ListArgs &a, int64_t t, const ui
   ok = __shfl_sync(0xffffffffu, ok, 0);
   pos = (unsigned long long)__shfl_sync(0xffffffffu, (long long)pos, 0);
   if (ok && cnt > 0) {
-    copy_out(a, slab, cnt, a.chunk + 3ull * pos, lane, 32);
+    copy_out(a.inv, slab, cnt, a.chunk + 3ull * pos, lane, 32);
   }
   __syncwarp();
 }
 
 // Warp-level walk of the tests [i0, i1) of B vertex x, whose probe-side row
 // is [pb, pe); k0 is the seed edge holding test i0 (found by binary search
-// when ~0).  For each test: z = the scanned element, member(z) = B[z]; hits
-// are appended as sorted original ids to the slab, at positions reserved from
-// the warp's own count (kWarpSlab) or from the CTA's shared count *s_cnt.
-template <bool kWarpSlab, class Member>
+// when ~0).  For each test: z = the scanned element, member(z) = B[z].  Hits
+// go to the warp's own global slab as (original id of x, original id of y,
+// rank of z) at positions counted by wcnt (kEmit 0, warp tiers), or to the
+// warp's shared-memory buffer as (original id of y, rank of z), flushed to the
+// chunk whenever it could overflow in the next step (kEmit 1, CTA tiers: on a
+// failed flush the walk stops with o.failed set).
+template <int kEmit, class Member>
 __device__ __forceinline__ void scan_items(const ListArgs &a, uint64_t pb, uint64_t pe, uint64_t k0,
                                            uint64_t i0, uint64_t i1, uint32_t inv_x,
-                                           Member member, uint32_t *slab, uint32_t *s_cnt,
+                                           Member member, uint32_t *slab, WarpOut &o,
                                            uint32_t &wcnt, unsigned long long &probes) {
   if (i0 >= i1) return;
   const int lane = threadIdx.x & 31;
@@ -299,21 +367,23 @@ __device__ __forceinline__ void scan_items(const ListArgs &a, uint64_t pb, uint6
   auto emit = [&](bool hit, uint32_t iyj, uint32_t z) {
     const unsigned hm = __ballot_sync(0xffffffffu, hit);
     if (!hm) return;
-    uint32_t basepos = 0;
-    if (kWarpSlab) {
+    uint32_t basepos;
+    if (kEmit == 0) {
       basepos = wcnt;
       wcnt += __popc(hm);
     } else {
-      const int leader = __ffs(hm) - 1;
-      if (lane == leader) basepos = atomicAdd(s_cnt, (uint32_t)__popc(hm));
-      basepos = __shfl_sync(0xffffffffu, basepos, leader);
+      basepos = o.cnt;
+      o.cnt += __popc(hm);
     }
     if (hit) {
-      // z stays a rank here; copy_out translates it off the critical path
       const uint32_t r = basepos + __popc(hm & lt);
-      slab[3 * r + 0] = inv_x;
-      slab[3 * r + 1] = iyj;
-      slab[3 * r + 2] = z;
+      if (kEmit == 0) {
+        slab[3 * r + 0] = inv_x;
+        slab[3 * r + 1] = iyj;
+        slab[3 * r + 2] = z;
+      } else {
+        reinterpret_cast<uint2 *>(o.buf)[r] = make_uint2(iyj, z);
+      }
     }
   };
   uint64_t base = i0;
@@ -337,45 +407,49 @@ __device__ __forceinline__ void scan_items(const ListArgs &a, uint64_t pb, uint6
       // 128 tests of an iteration at once.
       const uint64_t lo = Aj, hi = Aj + run;
       for (uint64_t q0 = lo & ~3ull; q0 < hi; q0 += 128) {
+        if (kEmit == 1 && o.cnt > kWarpBuf - kWarpStep) {
+          // every test before this iteration's first one has its hits in buf
+          if (!warp_commit(a, o, inv_x, base + (q0 > lo ? q0 - lo : 0), probes)) return;
+        }
         const uint64_t q = q0 + 4 * lane;
         uint4 v = make_uint4(0, 0, 0, 0);
         if (q < hi) v = *reinterpret_cast<const uint4 *>(a.out_adj + q);
         const uint32_t z[4] = {v.x, v.y, v.z, v.w};
-        uint32_t hits = 0, nh = 0;
+        // the iteration's tests: [max(q0, lo), min(q0 + 128, hi)), counted once
+        if (lane == 0) probes += (q0 + 128 < hi ? q0 + 128 : hi) - (q0 > lo ? q0 : lo);
+        bool hit[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const bool act = q + u >= lo && q + u < hi;
-          probes += act ? 1 : 0;
-          if (act && member(z[u])) {
-            hits |= 1u << u;
-            ++nh;
-          }
-        }
-        // warp prefix of hit counts -> slab positions
-        uint32_t incl = nh;
+        for (int u = 0; u < 4; ++u) hit[u] = q + u >= lo && q + u < hi && member(z[u]);
+        // positions: the hits of element u of all lanes, u = 0..3, one after
+        // the other (the order of triangles is free)
+        unsigned hm[4];
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-          const uint32_t o = __shfl_up_sync(0xffffffffu, incl, d);
-          if (lane >= d) incl += o;
-        }
-        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        for (int u = 0; u < 4; ++u) hm[u] = __ballot_sync(0xffffffffu, hit[u]);
+        const uint32_t c0 = __popc(hm[0]), c1 = __popc(hm[1]), c2 = __popc(hm[2]);
+        const uint32_t total = c0 + c1 + c2 + __popc(hm[3]);
         if (total == 0) continue;
-        uint32_t basepos = 0;
-        if (kWarpSlab) {
+        uint32_t basepos;
+        if (kEmit == 0) {
           basepos = wcnt;
           wcnt += total;
         } else {
-          if (lane == 31) basepos = atomicAdd(s_cnt, total);
-          basepos = __shfl_sync(0xffffffffu, basepos, 31);
+          basepos = o.cnt;
+          o.cnt += total;
         }
-        uint32_t r = basepos + incl - nh;
+        const uint32_t start[4] = {basepos, basepos + c0, basepos + c0 + c1,
+                                   basepos + c0 + c1 + c2};
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          if (hits & (1u << u)) {
-            slab[3 * r + 0] = inv_x;
-            slab[3 * r + 1] = iyj;
-            slab[3 * r + 2] = z[u];
-            ++r;
+          if (hit[u]) {
+            // z stays a rank here; the copy to the chunk translates it
+            const uint32_t r = start[u] + __popc(hm[u] & lt);
+            if (kEmit == 0) {
+              slab[3 * r + 0] = inv_x;
+              slab[3 * r + 1] = iyj;
+              slab[3 * r + 2] = z[u];
+            } else {
+              reinterpret_cast<uint2 *>(o.buf)[r] = make_uint2(iyj, z[u]);
+            }
           }
         }
       }
@@ -383,6 +457,9 @@ __device__ __forceinline__ void scan_items(const ListArgs &a, uint64_t pb, uint6
       continue;
     }
     // Short segments: one step of up to 32 tests spread over several lists.
+    if (kEmit == 1 && o.cnt > kWarpBuf - kWarpStep) {
+      if (!warp_commit(a, o, inv_x, base, probes)) return;
+    }
     uint64_t lim = base + 32;
     if (lim > i1) lim = i1;
     if (lim > Elast) lim = Elast;
@@ -415,6 +492,7 @@ __global__ void __launch_bounds__(kWarpThreads, 4) k_list_warp(ListArgs a) {
   uint32_t *H = sm + wid * SLOTS;
   const uint64_t gwarp = (uint64_t)blockIdx.x * (kWarpThreads / 32) + wid;
   uint32_t *slab = a.slabs + gwarp * a.slab_cap * 3;
+  WarpOut nout{nullptr, 0, 0, 0, false};  // unused by the global-slab path
   for (;;) {
     int64_t t = 0;
     if (lane == 0) t = fetch_task(a.ctl, a);
@@ -434,9 +512,8 @@ __global__ void __launch_bounds__(kWarpThreads, 4) k_list_warp(ListArgs a) {
       __syncwarp();
       for (uint64_t q = pb + lane; q < pe; q += 32) hash_insert(H, lg, a.padj[q]);
       __syncwarp();
-      scan_items<true>(a, pb, pe, pb, a.WP[pb], a.WP[pe], a.inv[x],
-                       [&](uint32_t z) { return hash_find(H, lg, z); }, slab, nullptr, cnt,
-                       probes);
+      scan_items<0>(a, pb, pe, pb, a.WP[pb], a.WP[pe], a.inv[x],
+                    [&](uint32_t z) { return hash_find(H, lg, z); }, slab, nout, cnt, probes);
       __syncwarp();
     }
 #pragma unroll
@@ -454,13 +531,15 @@ __global__ void __launch_bounds__(kWarpThreads, 4) k_list_warp(ListArgs a) {
 
 template <int THREADS, int TIER>
 __global__ void __launch_bounds__(THREADS, TIER == 3 ? 1 : 4) k_list_cta(ListArgs a) {
-  extern __shared__ uint32_t sm[];  // bitmap or hash table
-  __shared__ int64_t s_t;
-  __shared__ uint32_t s_x, s_cnt, s_ok, s_mode, s_lg;
-  __shared__ unsigned long long s_pos, s_probes, s_a, s_b;
-  uint32_t *slab = a.slabs + (uint64_t)blockIdx.x * a.slab_cap * 3;
+  // probe structure (bitmap, hash or filter) | one output buffer per warp
+  extern __shared__ __align__(16) uint32_t sm[];
+  constexpr uint32_t kProbeWords = (TIER == 2 ? kMidProbeBytes : kLargeProbeBytes) / 4;
+  __shared__ unsigned long long s_a, s_b;
+  __shared__ uint32_t s_x, s_ok, s_mode, s_lg;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   constexpr int kWarps = THREADS / 32;
+  WarpOut o{sm + kProbeWords + (uint32_t)wid * 2 * kWarpBuf, 0, 0, 0, false};
+  uint32_t unused = 0;
   const bool use_bitmap = TIER == 3 && a.n <= kBitmapMaxN;
   if (use_bitmap) {
     const uint32_t words = (a.n + 31) >> 5;
@@ -468,22 +547,15 @@ __global__ void __launch_bounds__(THREADS, TIER == 3 ? 1 : 4) k_list_cta(ListArg
   }
   for (;;) {
     if (threadIdx.x == 0) {
-      const int64_t t = fetch_task(a.ctl, a);
-      s_t = t;
-      if (t >= 0) {
-        // x = the vertex owning task t; the task is its piece t - prefix[x]
-        const uint32_t x = a.task_x[t];
-        const uint64_t piece = (uint64_t)t - a.piece_prefix[x - a.x_begin];
-        const uint64_t pb = a.poff[x], pe = a.poff[x + 1];
-        const uint64_t p = pe - pb;
-        const uint64_t w0 = a.WP[pb], w1 = a.WP[pe];
-        const uint64_t pw = piece_work(TIER, p);
-        const uint64_t ia = w0 + piece * pw;
+      uint32_t x = 0;
+      uint64_t ia = 0, ib = 0;
+      const bool ok = fetch_range(a, x, ia, ib);
+      s_ok = ok;
+      if (ok) {
+        const uint64_t p = a.poff[x + 1] - a.poff[x];
         s_x = x;
         s_a = ia;
-        s_b = (ia + pw < w1) ? ia + pw : w1;
-        s_cnt = 0;
-        s_probes = 0;
+        s_b = ib;
         s_lg = 6;
         if (use_bitmap) {
           s_mode = 0;
@@ -506,8 +578,7 @@ __global__ void __launch_bounds__(THREADS, TIER == 3 ? 1 : 4) k_list_cta(ListArg
       }
     }
     __syncthreads();
-    const int64_t t = s_t;
-    if (t < 0) break;
+    if (!s_ok) break;
     const uint32_t x = s_x;
     const uint64_t pb = a.poff[x], pe = a.poff[x + 1];
     const uint32_t mode = s_mode;
@@ -536,7 +607,7 @@ __global__ void __launch_bounds__(THREADS, TIER == 3 ? 1 : 4) k_list_cta(ListArg
       }
     }
     __syncthreads();
-    // the piece's tests, split into one contiguous range per warp
+    // the range's tests, split into one contiguous part per warp
     const uint64_t ia = s_a, ib = s_b;
     const uint64_t per = (((ib - ia) + kWarps - 1) / kWarps + 31) & ~31ull;
     uint64_t wa = ia + (uint64_t)wid * per;
@@ -545,44 +616,55 @@ __global__ void __launch_bounds__(THREADS, TIER == 3 ? 1 : 4) k_list_cta(ListArg
     if (wb > ib) wb = ib;
     const uint32_t inv_x = a.inv[x];
     unsigned long long probes = 0;
-    uint32_t unused = 0;
+    o.cnt = 0;
+    o.safe = wa;
+    o.probes_safe = 0;
+    o.failed = false;
     if (mode == 0) {
-      scan_items<false>(a, pb, pe, ~0ull, wa, wb, inv_x,
-                        [&](uint32_t z) { return ((sm[z >> 5] >> (z & 31)) & 1u) != 0; }, slab,
-                        &s_cnt, unused, probes);
+      scan_items<1>(a, pb, pe, ~0ull, wa, wb, inv_x,
+                    [&](uint32_t z) { return ((sm[z >> 5] >> (z & 31)) & 1u) != 0; }, nullptr,
+                    o, unused, probes);
     } else if (mode == 1) {
-      scan_items<false>(a, pb, pe, ~0ull, wa, wb, inv_x,
-                        [&](uint32_t z) { return bucket_find(sm, lg - 2, z); }, slab, &s_cnt,
-                        unused, probes);
+      scan_items<1>(a, pb, pe, ~0ull, wa, wb, inv_x,
+                    [&](uint32_t z) { return bucket_find(sm, lg - 2, z); }, nullptr, o, unused,
+                    probes);
     } else if (mode == 3) {
       const uint32_t *gh = a.ghash + (uint64_t)blockIdx.x * kGHashSlots;
-      scan_items<false>(a, pb, pe, ~0ull, wa, wb, inv_x,
-                        [&](uint32_t z) {
-                          const uint32_t f = fslot(z);
-                          if (((sm[f >> 5] >> (f & 31)) & 1u) == 0) return false;
-                          return hash_find_global(gh, lg, z);
-                        },
-                        slab, &s_cnt, unused, probes);
+      scan_items<1>(a, pb, pe, ~0ull, wa, wb, inv_x,
+                    [&](uint32_t z) {
+                      const uint32_t f = fslot(z);
+                      if (((sm[f >> 5] >> (f & 31)) & 1u) == 0) return false;
+                      return hash_find_global(gh, lg, z);
+                    },
+                    nullptr, o, unused, probes);
     } else {
-      scan_items<false>(a, pb, pe, ~0ull, wa, wb, inv_x,
-                        [&](uint32_t z) {
-                          uint64_t lo = pb, hi = pe;
-                          while (lo < hi) {
-                            const uint64_t mid = (lo + hi) >> 1;
-                            if (a.padj[mid] < z) lo = mid + 1; else hi = mid;
-                          }
-                          return lo < pe && a.padj[lo] == z;
-                        },
-                        slab, &s_cnt, unused, probes);
+      scan_items<1>(a, pb, pe, ~0ull, wa, wb, inv_x,
+                    [&](uint32_t z) {
+                      uint64_t lo = pb, hi = pe;
+                      while (lo < hi) {
+                        const uint64_t mid = (lo + hi) >> 1;
+                        if (a.padj[mid] < z) lo = mid + 1; else hi = mid;
+                      }
+                      return lo < pe && a.padj[lo] == z;
+                    },
+                    nullptr, o, unused, probes);
     }
+    if (!o.failed) warp_commit(a, o, inv_x, wb, probes);
+    // commit the warp's tests before o.safe; queue the rest for the next launch
+    unsigned long long done = o.probes_safe;
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) probes += __shfl_down_sync(0xffffffffu, probes, d);
-    if (lane == 0) atomicAdd(&s_probes, probes);
+    for (int d = 16; d > 0; d >>= 1) done += __shfl_down_sync(0xffffffffu, done, d);
+    if (lane == 0) {
+      if (done) atomicAdd(&a.ctl->probes, done);
+      if (o.failed && o.safe < wb) {
+        const uint32_t r = atomicAdd(&a.ctl->n_retry_out, 1u);
+        a.rr_out[r] = RetryRange{o.safe, wb, x, 0};
+      }
+    }
     __syncthreads();
     if (mode == 0) {  // reset B
       for (uint64_t q = pb + threadIdx.x; q < pe; q += THREADS) sm[a.padj[q] >> 5] = 0;
     }
-    commit_task(a.ctl, a, t, slab, s_cnt, s_probes, &s_ok, &s_pos);
   }
 }
 
@@ -752,7 +834,7 @@ int occupancy_grid(K kernel, int threads, int smem) {
 
 constexpr int kSmemSmall = kSmallSlots * 4 * (kWarpThreads / 32);
 constexpr int kSmemMedium = kMediumSlots * 4 * (kWarpThreads / 32);
-constexpr int kSmemMid = kMidSlots * 4;
+constexpr int kSmemMid = kMidSmemBytes;
 
 }  // namespace
 
@@ -811,8 +893,8 @@ int tier_grid(int tier) {
 
 uint64_t list_fixed_bytes(uint64_t chunk_bytes) {
   uint64_t slab = 0;
-  for (int t = 0; t < kTiers; ++t) {
-    const uint64_t w = (uint64_t)tier_grid(t) * (t < 2 ? (kWarpThreads / 32) : 1) * slab_cap(t);
+  for (int t = 0; t < 2; ++t) {  // the warp tiers' global slabs
+    const uint64_t w = (uint64_t)tier_grid(t) * (kWarpThreads / 32) * slab_cap(t);
     slab = w > slab ? w : slab;
   }
   return 2 * (chunk_bytes / 12) * 12 + slab * 12 +

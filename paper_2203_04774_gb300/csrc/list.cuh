@@ -35,34 +35,49 @@ __host__ __device__ inline uint64_t piece_work(int tier, uint64_t p) {
   return w > kPieceMax ? kPieceMax : w;
 }
 // Shared-memory probe structures of the large kernel.
-constexpr uint32_t kBitmapMaxN = 1572864u;               // 192 KiB bitmap over ranks
+constexpr uint32_t kBitmapMaxN = 1u << 20;               // 128 KiB bitmap over ranks
 constexpr uint32_t kHashMaxSlots = 32768u;               // 128 KiB hash table
 // Hubs too large for the shared-memory table when n > kBitmapMaxN: a 2^20-bit
 // shared-memory filter over hashed ranks in front of a per-CTA hash table of
 // kGHashSlots slots in global memory (p <= kGHashSlots / 2).
 constexpr uint32_t kFilterWords = 1u << 15;
 constexpr uint32_t kGHashSlots = 1u << 18;
-constexpr int kLargeSmemBytes = (int)(kBitmapMaxN / 8);  // >= kHashMaxSlots * 4
-// Triangles a task can produce (bounded by its work): per warp for the warp
-// tiers, per CTA for the mid and large tiers.
+// Output of the CTA tiers: each warp stages its hits as (original id of y,
+// rank of z) pairs in a shared-memory buffer of kWarpBuf entries and copies
+// them to the chunk itself when fewer than kWarpStep free entries are left
+// (one step adds at most kWarpStep hits) and at the end of its range.
+constexpr uint32_t kWarpBuf = 352;  // 4 mid CTAs (56 KiB each) per SM
+constexpr uint32_t kWarpStep = 128;
+constexpr int kMidProbeBytes = kMidSlots * 4;
+constexpr int kLargeProbeBytes = (int)(kBitmapMaxN / 8);  // = kHashMaxSlots * 4 = kFilterWords * 4
+constexpr int kMidSmemBytes = kMidProbeBytes + (kMidThreads / 32) * (int)kWarpBuf * 8;
+constexpr int kLargeSmemBytes = kLargeProbeBytes + (kLargeThreads / 32) * (int)kWarpBuf * 8;
+// Triangles a warp-tier task can produce (bounded by its work): the size of
+// each warp's global slab.  A chunk must hold at least that many.
 constexpr uint64_t kSlabCapWarp = 2 * kWarpWork;
-constexpr uint64_t kSlabCapMid = kMidPiece;
-constexpr uint64_t kSlabCapLarge = kPieceMax;
-constexpr uint64_t kSlabCap = kSlabCapLarge;
-__host__ __device__ inline uint64_t slab_cap(int tier) {
-  return tier < 2 ? kSlabCapWarp : (tier == 2 ? kSlabCapMid : kSlabCapLarge);
-}
+constexpr uint64_t kSlabCap = kSlabCapWarp;
+__host__ __device__ inline uint64_t slab_cap(int tier) { return tier < 2 ? kSlabCapWarp : 0; }
 
-// Device control block of one listing launch.
+// Device control block of one listing launch.  Reservations are atomic adds
+// to `cursor`, so the successful ones form the prefix [start, first_fail) of
+// the chunk (or [start, cursor) when none failed).
+// The cursor, hit by every reservation, has a 128-byte line of its own.
 struct ListCtl {
-  unsigned long long cursor;     // chunk slots reserved (may pass the capacity)
-  unsigned long long valid_end;  // end of the committed prefix of the chunk
-  unsigned long long triangles;  // triangles committed
-  unsigned long long probes;     // membership tests of committed tasks
-  uint32_t overflow;             // a reservation did not fit
-  uint32_t fetch;                // task fetch counter
-  uint32_t n_retry_out;          // tasks queued for the next launch
-  uint32_t pad;
+  unsigned long long cursor;      // chunk slots reserved (may pass the capacity)
+  unsigned long long pad0[15];
+  unsigned long long first_fail;  // smallest position of a reservation that did not fit
+  unsigned long long probes;      // membership tests of committed work
+  uint32_t overflow;              // a reservation did not fit
+  uint32_t fetch;                 // task fetch counter
+  uint32_t n_retry_out;           // tasks / ranges queued for the next launch
+  uint32_t pad1;
+};
+
+// Retry record of the CTA tiers: the tests [i0, i1) of B vertex x that a warp
+// could not commit because the chunk was full.
+struct RetryRange {
+  uint64_t i0, i1;
+  uint32_t x, pad;
 };
 
 struct ListArgs {
@@ -90,9 +105,11 @@ struct ListArgs {
   uint64_t chunk_cap;            // triangles
   uint32_t *slabs;               // per-CTA staging, slab_cap triangles each
   uint64_t slab_cap;
-  const uint32_t *retry_in;      // tasks left over by the previous launch
-  uint32_t n_retry;
+  const uint32_t *retry_in;      // warp tiers: tasks left over by the previous launch
+  uint32_t n_retry;              // entries in retry_in / rr_in
   uint32_t *retry_out;
+  const RetryRange *rr_in;       // CTA tiers: ranges left over by the previous launch
+  RetryRange *rr_out;
   uint64_t fresh_base;           // first task not yet fetched
   uint64_t n_tasks;
 };
