@@ -233,10 +233,12 @@ tl_status list_impl(tl_graph *G, int alg, uint32_t xb, uint32_t xe, size_t chunk
   tl::ListCtl *hc = G->pctl->h;
   uint32_t *chunk[2] = {G->chunks.as<uint32_t>(), G->chunks.as<uint32_t>() + 3 * cap};
   uint32_t *retry[2] = {G->retry.as<uint32_t>(), G->retry.as<uint32_t>() + max_tasks};
-  // CTA tiers: each launch queues at most one range per resident warp, plus
-  // the ranges it did not fetch
-  const uint64_t warps_cta = std::max<uint64_t>((uint64_t)tl::tier_grid(2) * (tl::kMidThreads / 32),
-                                                (uint64_t)tl::tier_grid(3) * (tl::kLargeThreads / 32));
+  // CTA tiers: each launch queues at most one range per resident warp and
+  // piece; a CTA runs at most two pieces after the chunk fills (the current
+  // one and the one it had already fetched); plus the ranges it did not fetch
+  const uint64_t warps_cta =
+      2 * std::max<uint64_t>((uint64_t)tl::tier_grid(2) * (tl::kMidThreads / 32),
+                             (uint64_t)tl::tier_grid(3) * (tl::kLargeThreads / 32));
   auto rr_half = [&](int h) { return G->rretry.as<tl::RetryRange>() + h * G->rretry_cap; };
   auto reserve_ranges = [&](int in_half, uint64_t n_in, uint64_t need) {
     if (need <= G->rretry_cap) return;

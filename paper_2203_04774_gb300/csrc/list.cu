@@ -534,8 +534,10 @@ __global__ void __launch_bounds__(THREADS, TIER == 3 ? 1 : 4) k_list_cta(ListArg
   // probe structure (bitmap, hash or filter) | one output buffer per warp
   extern __shared__ __align__(16) uint32_t sm[];
   constexpr uint32_t kProbeWords = (TIER == 2 ? kMidProbeBytes : kLargeProbeBytes) / 4;
+  // the next piece of work, fetched by the first warp done with the current
+  // one while the others finish (or by thread 0 before the first)
   __shared__ unsigned long long s_a, s_b;
-  __shared__ uint32_t s_x, s_ok, s_mode, s_lg;
+  __shared__ uint32_t s_x, s_ok, s_mode, s_lg, s_fetcher;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   constexpr int kWarps = THREADS / 32;
   WarpOut o{sm + kProbeWords + (uint32_t)wid * 2 * kWarpBuf, 0, 0, 0, false};
@@ -545,44 +547,48 @@ __global__ void __launch_bounds__(THREADS, TIER == 3 ? 1 : 4) k_list_cta(ListArg
     const uint32_t words = (a.n + 31) >> 5;
     for (uint32_t i = threadIdx.x; i < words; i += THREADS) sm[i] = 0;
   }
-  for (;;) {
-    if (threadIdx.x == 0) {
-      uint32_t x = 0;
-      uint64_t ia = 0, ib = 0;
-      const bool ok = fetch_range(a, x, ia, ib);
-      s_ok = ok;
-      if (ok) {
-        const uint64_t p = a.poff[x + 1] - a.poff[x];
-        s_x = x;
-        s_a = ia;
-        s_b = ib;
-        s_lg = 6;
-        if (use_bitmap) {
-          s_mode = 0;
-        } else {
-          // mid tier: load <= 1/4, so most lookups end at the first bucket
-          const uint32_t max_slots = TIER == 2 ? (uint32_t)kMidSlots : kHashMaxSlots;
-          const uint64_t want = TIER == 2 ? 4 * p : 2 * p;
-          uint32_t lg = 6;
-          while ((1ull << lg) < want && (1u << lg) < max_slots) ++lg;
-          s_lg = lg;
-          s_mode = (2 * p <= (1ull << lg)) ? 1 : 2;  // 2: too large, binary search
-          if (TIER == 3 && s_mode == 2 && a.ghash && 2 * p <= kGHashSlots) {
-            // 3: shared-memory filter + this CTA's hash table in global memory
-            lg = 6;
-            while ((1ull << lg) < 2 * p) ++lg;
-            s_lg = lg;
-            s_mode = 3;
-          }
-        }
-      }
+  auto fetch_next = [&]() {  // one thread
+    uint32_t x = 0;
+    uint64_t ia = 0, ib = 0;
+    const bool ok = fetch_range(a, x, ia, ib);
+    s_ok = ok;
+    if (!ok) return;
+    const uint64_t p = a.poff[x + 1] - a.poff[x];
+    s_x = x;
+    s_a = ia;
+    s_b = ib;
+    s_lg = 6;
+    if (use_bitmap) {
+      s_mode = 0;
+      return;
     }
+    // mid tier: load <= 1/4, so most lookups end at the first bucket
+    const uint32_t max_slots = TIER == 2 ? (uint32_t)kMidSlots : kHashMaxSlots;
+    const uint64_t want = TIER == 2 ? 4 * p : 2 * p;
+    uint32_t lg = 6;
+    while ((1ull << lg) < want && (1u << lg) < max_slots) ++lg;
+    s_lg = lg;
+    s_mode = (2 * p <= (1ull << lg)) ? 1 : 2;  // 2: too large, binary search
+    if (TIER == 3 && s_mode == 2 && a.ghash && 2 * p <= kGHashSlots) {
+      // 3: shared-memory filter + this CTA's hash table in global memory
+      lg = 6;
+      while ((1ull << lg) < 2 * p) ++lg;
+      s_lg = lg;
+      s_mode = 3;
+    }
+  };
+  if (threadIdx.x == 0) {
+    s_fetcher = 0;
+    fetch_next();
+  }
+  for (;;) {
     __syncthreads();
     if (!s_ok) break;
     const uint32_t x = s_x;
     const uint64_t pb = a.poff[x], pe = a.poff[x + 1];
     const uint32_t mode = s_mode;
     const int lg = (int)s_lg;
+    const uint64_t ia = s_a, ib = s_b;
     // build B: the probe set P_x
     if (mode == 0) {
       for (uint64_t q = pb + threadIdx.x; q < pe; q += THREADS) {
@@ -608,7 +614,6 @@ __global__ void __launch_bounds__(THREADS, TIER == 3 ? 1 : 4) k_list_cta(ListArg
     }
     __syncthreads();
     // the range's tests, split into one contiguous part per warp
-    const uint64_t ia = s_a, ib = s_b;
     const uint64_t per = (((ib - ia) + kWarps - 1) / kWarps + 31) & ~31ull;
     uint64_t wa = ia + (uint64_t)wid * per;
     uint64_t wb = wa + per;
@@ -660,8 +665,12 @@ __global__ void __launch_bounds__(THREADS, TIER == 3 ? 1 : 4) k_list_cta(ListArg
         const uint32_t r = atomicAdd(&a.ctl->n_retry_out, 1u);
         a.rr_out[r] = RetryRange{o.safe, wb, x, 0};
       }
+      // every thread has read the current piece's s_* (before the barrier
+      // that ended the build); the first warp here fetches the next piece
+      if (atomicExch(&s_fetcher, 1u) == 0) fetch_next();
     }
     __syncthreads();
+    if (threadIdx.x == 0) s_fetcher = 0;
     if (mode == 0) {  // reset B
       for (uint64_t q = pb + threadIdx.x; q < pe; q += THREADS) sm[a.padj[q] >> 5] = 0;
     }
