@@ -58,7 +58,7 @@ struct tl_graph {
   tl::DeviceGraph g;
   // listing workspace
   tl::DevBuf wseed, WP, ctl, chunks, slabs, retry, rretry, ghash;
-  uint64_t rretry_cap = 0;  // RetryRange records per half of rretry
+  uint64_t rretry_cap = 0;  // RetryPiece records per half of rretry
   // per-vertex classification (tiers 0, 1: weights and flags; tiers 2, 3: pieces),
   // their prefixes, and the compacted vertex lists of tiers 0 and 1
   tl::DevBuf tw[2], tf[2], tpref[2], tpos[2], tx[2], twp[2], tstart[2], pieces[2],
@@ -233,21 +233,19 @@ tl_status list_impl(tl_graph *G, int alg, uint32_t xb, uint32_t xe, size_t chunk
   tl::ListCtl *hc = G->pctl->h;
   uint32_t *chunk[2] = {G->chunks.as<uint32_t>(), G->chunks.as<uint32_t>() + 3 * cap};
   uint32_t *retry[2] = {G->retry.as<uint32_t>(), G->retry.as<uint32_t>() + max_tasks};
-  // CTA tiers: each launch queues at most one range per resident warp and
-  // piece; a CTA runs at most two pieces after the chunk fills (the current
-  // one and the one it had already fetched); plus the ranges it did not fetch
-  const uint64_t warps_cta =
-      2 * std::max<uint64_t>((uint64_t)tl::tier_grid(2) * (tl::kMidThreads / 32),
-                             (uint64_t)tl::tier_grid(3) * (tl::kLargeThreads / 32));
-  auto rr_half = [&](int h) { return G->rretry.as<tl::RetryRange>() + h * G->rretry_cap; };
+  // CTA tiers: a launch queues at most one record per CTA and piece, and a
+  // CTA runs at most two pieces after the chunk fills (the current one and
+  // the one it had already fetched); plus the records it did not fetch
+  const uint64_t warps_cta = 2 * std::max<uint64_t>(tl::tier_grid(2), tl::tier_grid(3));
+  auto rr_half = [&](int h) { return G->rretry.as<tl::RetryPiece>() + h * G->rretry_cap; };
   auto reserve_ranges = [&](int in_half, uint64_t n_in, uint64_t need) {
     if (need <= G->rretry_cap) return;
     const uint64_t cap2 = std::max<uint64_t>(need, 2 * G->rretry_cap);
     tl::DevBuf nb(s);
-    nb.reserve(2 * cap2 * sizeof(tl::RetryRange));
+    nb.reserve(2 * cap2 * sizeof(tl::RetryPiece));
     if (n_in)
-      TL_CUDA(cudaMemcpyAsync(nb.as<tl::RetryRange>() + in_half * cap2, rr_half(in_half),
-                              n_in * sizeof(tl::RetryRange), cudaMemcpyDeviceToDevice, s));
+      TL_CUDA(cudaMemcpyAsync(nb.as<tl::RetryPiece>() + in_half * cap2, rr_half(in_half),
+                              n_in * sizeof(tl::RetryPiece), cudaMemcpyDeviceToDevice, s));
     std::swap(G->rretry.p, nb.p);
     std::swap(G->rretry.bytes, nb.bytes);
     G->rretry_cap = cap2;
@@ -361,7 +359,7 @@ tl_status list_impl(tl_graph *G, int alg, uint32_t xb, uint32_t xe, size_t chunk
                                 cudaMemcpyDeviceToDevice, s));
       } else {
         TL_CUDA(cudaMemcpyAsync(rr_half(rsel ^ 1) + nr_out, rr_half(rsel) + used_retry,
-                                left * sizeof(tl::RetryRange), cudaMemcpyDeviceToDevice, s));
+                                left * sizeof(tl::RetryPiece), cudaMemcpyDeviceToDevice, s));
       }
       nr_out += (uint32_t)left;
     }

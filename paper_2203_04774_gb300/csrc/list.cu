@@ -271,18 +271,17 @@ __device__ __forceinline__ bool warp_commit(const ListArgs &a, WarpOut &o, uint3
   return true;
 }
 
-// Next piece of work of a CTA tier (thread 0): a retry range, else the next
-// fresh task's piece [ia, ib) of B vertex x.  False when the chunk is full or
-// no work is left.
-__device__ __forceinline__ bool fetch_range(const ListArgs &a, uint32_t &x, uint64_t &ia,
-                                            uint64_t &ib) {
+// Next piece of work of a CTA tier (thread 0): a retry piece (*retry set to
+// its record), else the next fresh task's piece [ia, ib) of B vertex x.
+// False when the chunk is full or no work is left.
+__device__ __forceinline__ bool fetch_piece(const ListArgs &a, uint32_t &x, uint64_t &ia,
+                                            uint64_t &ib, const RetryPiece *&retry) {
+  retry = nullptr;
   if (*(volatile uint32_t *)&a.ctl->overflow) return false;
   const uint32_t idx = atomicAdd(&a.ctl->fetch, 1u);
   if (idx < a.n_retry) {
-    const RetryRange r = a.rr_in[idx];
-    x = r.x;
-    ia = r.i0;
-    ib = r.i1;
+    retry = a.rr_in + idx;
+    x = retry->x;
     return true;
   }
   const uint64_t t = a.fresh_base + (idx - a.n_retry);
@@ -534,12 +533,13 @@ __global__ void __launch_bounds__(THREADS, TIER == 3 ? 1 : 4) k_list_cta(ListArg
   // probe structure (bitmap, hash or filter) | one output buffer per warp
   extern __shared__ __align__(16) uint32_t sm[];
   constexpr uint32_t kProbeWords = (TIER == 2 ? kMidProbeBytes : kLargeProbeBytes) / 4;
-  // the next piece of work, fetched by the first warp done with the current
-  // one while the others finish (or by thread 0 before the first)
-  __shared__ unsigned long long s_a, s_b;
-  __shared__ uint32_t s_x, s_ok, s_mode, s_lg, s_fetcher;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // the next piece of work (one test range per warp), fetched by the first
+  // warp done with the current one while the others finish (or by thread 0
+  // before the first); the ranges of warps stopped by a full chunk
   constexpr int kWarps = THREADS / 32;
+  __shared__ unsigned long long s_rng[kWarps][2], s_fail[kWarps][2];
+  __shared__ uint32_t s_x, s_ok, s_mode, s_lg, s_fetcher, s_nfail;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   WarpOut o{sm + kProbeWords + (uint32_t)wid * 2 * kWarpBuf, 0, 0, 0, false};
   uint32_t unused = 0;
   const bool use_bitmap = TIER == 3 && a.n <= kBitmapMaxN;
@@ -550,13 +550,26 @@ __global__ void __launch_bounds__(THREADS, TIER == 3 ? 1 : 4) k_list_cta(ListArg
   auto fetch_next = [&]() {  // one thread
     uint32_t x = 0;
     uint64_t ia = 0, ib = 0;
-    const bool ok = fetch_range(a, x, ia, ib);
+    const RetryPiece *rp = nullptr;
+    const bool ok = fetch_piece(a, x, ia, ib, rp);
     s_ok = ok;
     if (!ok) return;
+    if (rp) {  // the recorded ranges, one per warp
+      const uint32_t nr = rp->n;
+      for (int w = 0; w < kWarps; ++w) {
+        s_rng[w][0] = w < (int)nr ? rp->r[w][0] : 0;
+        s_rng[w][1] = w < (int)nr ? rp->r[w][1] : 0;
+      }
+    } else {  // the piece's tests, split evenly (32-aligned) over the warps
+      const uint64_t per = (((ib - ia) + kWarps - 1) / kWarps + 31) & ~31ull;
+      for (int w = 0; w < kWarps; ++w) {
+        const uint64_t u = ia + (uint64_t)w * per, v = u + per;
+        s_rng[w][0] = u < ib ? u : ib;
+        s_rng[w][1] = v < ib ? v : ib;
+      }
+    }
     const uint64_t p = a.poff[x + 1] - a.poff[x];
     s_x = x;
-    s_a = ia;
-    s_b = ib;
     s_lg = 6;
     if (use_bitmap) {
       s_mode = 0;
@@ -579,6 +592,7 @@ __global__ void __launch_bounds__(THREADS, TIER == 3 ? 1 : 4) k_list_cta(ListArg
   };
   if (threadIdx.x == 0) {
     s_fetcher = 0;
+    s_nfail = 0;
     fetch_next();
   }
   for (;;) {
@@ -588,7 +602,7 @@ __global__ void __launch_bounds__(THREADS, TIER == 3 ? 1 : 4) k_list_cta(ListArg
     const uint64_t pb = a.poff[x], pe = a.poff[x + 1];
     const uint32_t mode = s_mode;
     const int lg = (int)s_lg;
-    const uint64_t ia = s_a, ib = s_b;
+    const uint64_t wa = s_rng[wid][0], wb = s_rng[wid][1];  // this warp's tests
     // build B: the probe set P_x
     if (mode == 0) {
       for (uint64_t q = pb + threadIdx.x; q < pe; q += THREADS) {
@@ -613,12 +627,6 @@ __global__ void __launch_bounds__(THREADS, TIER == 3 ? 1 : 4) k_list_cta(ListArg
       }
     }
     __syncthreads();
-    // the range's tests, split into one contiguous part per warp
-    const uint64_t per = (((ib - ia) + kWarps - 1) / kWarps + 31) & ~31ull;
-    uint64_t wa = ia + (uint64_t)wid * per;
-    uint64_t wb = wa + per;
-    if (wa > ib) wa = ib;
-    if (wb > ib) wb = ib;
     const uint32_t inv_x = a.inv[x];
     unsigned long long probes = 0;
     o.cnt = 0;
@@ -662,15 +670,29 @@ __global__ void __launch_bounds__(THREADS, TIER == 3 ? 1 : 4) k_list_cta(ListArg
     if (lane == 0) {
       if (done) atomicAdd(&a.ctl->probes, done);
       if (o.failed && o.safe < wb) {
-        const uint32_t r = atomicAdd(&a.ctl->n_retry_out, 1u);
-        a.rr_out[r] = RetryRange{o.safe, wb, x, 0};
+        const uint32_t f = atomicAdd(&s_nfail, 1u);
+        s_fail[f][0] = o.safe;
+        s_fail[f][1] = wb;
       }
       // every thread has read the current piece's s_* (before the barrier
       // that ended the build); the first warp here fetches the next piece
       if (atomicExch(&s_fetcher, 1u) == 0) fetch_next();
     }
     __syncthreads();
-    if (threadIdx.x == 0) s_fetcher = 0;
+    if (threadIdx.x == 0) {
+      s_fetcher = 0;
+      const uint32_t nf = s_nfail;
+      if (nf) {  // one record for the piece's uncommitted ranges
+        RetryPiece *rp = a.rr_out + atomicAdd(&a.ctl->n_retry_out, 1u);
+        rp->x = x;
+        rp->n = nf;
+        for (uint32_t f = 0; f < nf; ++f) {
+          rp->r[f][0] = s_fail[f][0];
+          rp->r[f][1] = s_fail[f][1];
+        }
+        s_nfail = 0;
+      }
+    }
     if (mode == 0) {  // reset B
       for (uint64_t q = pb + threadIdx.x; q < pe; q += THREADS) sm[a.padj[q] >> 5] = 0;
     }

@@ -73,11 +73,14 @@ struct ListCtl {
   uint32_t pad1;
 };
 
-// Retry record of the CTA tiers: the tests [i0, i1) of B vertex x that a warp
-// could not commit because the chunk was full.
-struct RetryRange {
-  uint64_t i0, i1;
-  uint32_t x, pad;
+// Retry record of the CTA tiers: the tests of B vertex x that a CTA's warps
+// could not commit because the chunk was full, one range [r[i][0], r[i][1])
+// per warp that stopped.  A retry runs them as one piece (one build of B),
+// warp i taking range i.
+constexpr int kMaxRanges = kLargeThreads / 32;
+struct RetryPiece {
+  uint32_t x, n;
+  uint64_t r[kMaxRanges][2];
 };
 
 struct ListArgs {
@@ -108,8 +111,8 @@ struct ListArgs {
   const uint32_t *retry_in;      // warp tiers: tasks left over by the previous launch
   uint32_t n_retry;              // entries in retry_in / rr_in
   uint32_t *retry_out;
-  const RetryRange *rr_in;       // CTA tiers: ranges left over by the previous launch
-  RetryRange *rr_out;
+  const RetryPiece *rr_in;       // CTA tiers: pieces left over by the previous launch
+  RetryPiece *rr_out;
   uint64_t fresh_base;           // first task not yet fetched
   uint64_t n_tasks;
 };
