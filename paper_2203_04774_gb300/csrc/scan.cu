@@ -53,30 +53,35 @@ __global__ void __launch_bounds__(kScanThreads) k_tile_reduce(const T *__restric
   if (threadIdx.x == 0) partial[blockIdx.x] = tot;
 }
 
+// Tile element j lives at tile[pad(j)], one spare word after every 16: a
+// thread's 16 consecutive elements then start 17 words apart, so its
+// row-wise accesses hit distinct banks instead of one.
+__device__ __forceinline__ int pad(int j) { return j + (j >> 4); }
+
 template <class T>
 __global__ void __launch_bounds__(kScanThreads)
     k_tile_scan(const T *__restrict__ in, uint64_t *__restrict__ out, uint64_t n,
                 const uint64_t *__restrict__ tile_offset) {
-  __shared__ uint64_t tile[kScanTile];
+  __shared__ uint64_t tile[kScanTile + kScanTile / 16];
   const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     uint64_t idx = base + (uint64_t)i * kScanThreads + threadIdx.x;
-    tile[i * kScanThreads + threadIdx.x] = (idx < n) ? (uint64_t)in[idx] : 0;
+    tile[pad(i * kScanThreads + threadIdx.x)] = (idx < n) ? (uint64_t)in[idx] : 0;
   }
   __syncthreads();
   uint64_t v[kScanItems];
   uint64_t s = 0;
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
-    v[i] = tile[threadIdx.x * kScanItems + i];
+    v[i] = tile[pad(threadIdx.x * kScanItems + i)];
     s += v[i];
   }
   __shared__ uint64_t tot;
   uint64_t run = block_excl_scan(s, &tot) + (tile_offset ? tile_offset[blockIdx.x] : 0);
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
-    tile[threadIdx.x * kScanItems + i] = run;
+    tile[pad(threadIdx.x * kScanItems + i)] = run;
     run += v[i];
   }
   // out[n] = grand total, written by the thread holding element n-1.
@@ -84,14 +89,14 @@ __global__ void __launch_bounds__(kScanThreads)
     uint64_t first = base + (uint64_t)threadIdx.x * kScanItems;
     if (n - 1 >= first && n - 1 < first + kScanItems) {
       int i = (int)(n - 1 - first);
-      out[n] = tile[threadIdx.x * kScanItems + i] + v[i];
+      out[n] = tile[pad(threadIdx.x * kScanItems + i)] + v[i];
     }
   }
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     uint64_t idx = base + (uint64_t)i * kScanThreads + threadIdx.x;
-    if (idx < n) out[idx] = tile[i * kScanThreads + threadIdx.x];
+    if (idx < n) out[idx] = tile[pad(i * kScanThreads + threadIdx.x)];
   }
 }
 
