@@ -26,6 +26,7 @@ _lib = None
 
 APP = 0  # Algorithm 1, A++
 APM = 1  # Algorithm 2, A+-
+AMM = 2  # A--, the third variant (seed edge S2), cost C--
 LITERAL = 0
 SETS = 1
 

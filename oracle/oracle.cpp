@@ -135,12 +135,34 @@ void list_apm_literal(const Graph &g, uint32_t u_begin, uint32_t u_end, Sink &s,
   }
 }
 
-// The same two algorithms written as one sorted-list intersection per seed
+// A-- ("S2+n", the third variant the footnote of Sec. 2.1 names, seed edge
+// S2 = (v, w)), in the same boolean-array form: for each vertex v, mark N-_v
+// in B; for every w in N+_v and every u in N-_w, a set B[u] reports
+// {u, v, w}; reset B.  Vertex w is scanned once per predecessor v, so the
+// work is sum_w d-_w * d-_w = C-- (the mirror image of C++ under the reversed
+// ordering, hence the footnote's "equivalent to A++").
+void list_amm_literal(const Graph &g, uint32_t v_begin, uint32_t v_end, Sink &s,
+                      uint64_t &probes) {
+  std::vector<char> B(g.n, 0);
+  for (uint32_t v = v_begin; v < v_end; ++v) {
+    for (uint32_t u : g.in[v]) B[u] = 1;
+    for (uint32_t w : g.out[v]) {
+      for (uint32_t u : g.in[w]) {
+        ++probes;
+        if (B[u]) s.output(u, v, w);
+      }
+    }
+    for (uint32_t u : g.in[v]) B[u] = 0;
+  }
+}
+
+// The same algorithms written as one sorted-list intersection per seed
 // edge (Sec. 2.1, "neighborhood intersection"): A++ seeds on the long edge
 // L = (u, w) and intersects N+_u with N-_w; A+- seeds on the first short edge
-// S1 = (u, v) and intersects N+_u with N+_v.  std::set_intersection does the
-// work; "probes" here counts the scanned list (N+_u resp. N+_v) so that it is
-// comparable with the literal form.
+// S1 = (u, v) and intersects N+_u with N+_v; A-- seeds on the second short
+// edge S2 = (v, w) and intersects N-_v with N-_w.  std::set_intersection does
+// the work; "probes" here counts the scanned list (N+_u, N+_v resp. N-_w) so
+// that it is comparable with the literal form.
 void list_app_sets(const Graph &g, uint32_t w_begin, uint32_t w_end, Sink &s,
                    uint64_t &probes) {
   std::vector<uint32_t> common;
@@ -165,6 +187,20 @@ void list_apm_sets(const Graph &g, uint32_t u_begin, uint32_t u_end, Sink &s,
                             g.out[v].end(), std::back_inserter(common));
       probes += g.out[v].size();
       for (uint32_t w : common) s.output(u, v, w);
+    }
+  }
+}
+
+void list_amm_sets(const Graph &g, uint32_t v_begin, uint32_t v_end, Sink &s,
+                   uint64_t &probes) {
+  std::vector<uint32_t> common;
+  for (uint32_t v = v_begin; v < v_end; ++v) {
+    for (uint32_t w : g.out[v]) {
+      common.clear();
+      std::set_intersection(g.in[v].begin(), g.in[v].end(), g.in[w].begin(), g.in[w].end(),
+                            std::back_inserter(common));
+      probes += g.in[w].size();
+      for (uint32_t u : common) s.output(u, v, w);
     }
   }
 }
@@ -226,27 +262,28 @@ int or_order_apply(void *h, const uint32_t *rank) {
 
 // Cost induced by the ordering (Definition of Sec. 3.1):
 //   alg 0: C++ = sum_u d+_u * d+_u      alg 1: C+- = sum_u d+_u * d-_u
+//   alg 2: C-- = sum_u d-_u * d-_u (A--, by the same counting as Property 1)
 uint64_t or_cost(const void *h, int alg) {
   const Graph *g = static_cast<const Graph *>(h);
   uint64_t c = 0;
   for (uint32_t x = 0; x < g->n; ++x) {
     uint64_t dp = g->out[x].size(), dm = g->in[x].size();
-    c += (alg == 0) ? dp * dp : dp * dm;
+    c += (alg == 0) ? dp * dp : (alg == 1 ? dp * dm : dm * dm);
   }
   return c;
 }
 
-// List triangles with Algorithm 1 (alg 0) or Algorithm 2 (alg 1), in the
-// literal boolean-array form (mode 0) or the set-intersection form (mode 1).
-// The outer loop runs over ranks [seed_begin, seed_end) (pass 0 and n for
-// the whole graph; a sub-range lists the triangles whose third vertex (A++)
-// or first vertex (A+-) lies in it).  Triples go to buf[3*cap] when buf is
+// List triangles with Algorithm 1 (alg 0), Algorithm 2 (alg 1) or A-- (alg
+// 2), in the literal boolean-array form (mode 0) or the set-intersection form
+// (mode 1).  The outer loop runs over ranks [seed_begin, seed_end) (pass 0
+// and n for the whole graph; a sub-range lists the triangles whose third
+// vertex (A++), first vertex (A+-) or middle vertex (A--) lies in it).  Triples go to buf[3*cap] when buf is
 // not null.
 int or_list(const void *h, int alg, int mode, uint32_t seed_begin, uint32_t seed_end,
             uint32_t *buf, uint64_t cap, uint64_t *count, uint64_t *hash,
             uint64_t *probes) {
   const Graph *g = static_cast<const Graph *>(h);
-  if (alg < 0 || alg > 1 || mode < 0 || mode > 1) return 1;
+  if (alg < 0 || alg > 2 || mode < 0 || mode > 1) return 1;
   if (seed_end > g->n || seed_begin > seed_end) return 1;
   Sink s;
   s.buf = buf;
@@ -257,6 +294,8 @@ int or_list(const void *h, int alg, int mode, uint32_t seed_begin, uint32_t seed
   if (alg == 0 && mode == 1) list_app_sets(*g, seed_begin, seed_end, s, p);
   if (alg == 1 && mode == 0) list_apm_literal(*g, seed_begin, seed_end, s, p);
   if (alg == 1 && mode == 1) list_apm_sets(*g, seed_begin, seed_end, s, p);
+  if (alg == 2 && mode == 0) list_amm_literal(*g, seed_begin, seed_end, s, p);
+  if (alg == 2 && mode == 1) list_amm_sets(*g, seed_begin, seed_end, s, p);
   if (count) *count = s.count;
   if (hash) *hash = s.hash;
   if (probes) *probes = p;

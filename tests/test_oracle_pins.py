@@ -62,7 +62,7 @@ def test_fig3_triangles_brute_force():
     tri = _pins.brute_force_triangles(7, e)
     assert [tuple("abcdefg"[i] for i in t) for t in tri] == [
         ("a", "b", "e"), ("a", "d", "e"), ("b", "c", "g")]
-    for alg in (oracle.APP, oracle.APM):
+    for alg in (oracle.APP, oracle.APM, oracle.AMM):
         t, cnt, _, _ = g.list(alg)
         assert _as_set(t) == set(tri) and cnt == 3
 
@@ -101,7 +101,8 @@ def test_complete_graph_closed_forms(n):
         g.order_apply(rank)
         assert g.cost(oracle.APP) == cpp
         assert g.cost(oracle.APM) == cpm
-        for alg in (oracle.APP, oracle.APM):
+        assert g.cost(oracle.AMM) == cpp  # d-_v = rank of v, as d+ mirrored
+        for alg in (oracle.APP, oracle.APM, oracle.AMM):
             for mode in (oracle.LITERAL, oracle.SETS):
                 _, cnt, _, probes = g.list(alg, mode, store=False)
                 assert cnt == tri
@@ -114,9 +115,9 @@ def test_star_costs():
     g = oracle.Graph(n, synth.star(n, hub=0))
     last = np.array([n - 1] + list(range(n - 1)), dtype=np.uint32)  # hub ranked last
     g.order_apply(last)
-    assert (g.cost(oracle.APP), g.cost(oracle.APM)) == (n - 1, 0)
+    assert (g.cost(oracle.APP), g.cost(oracle.APM), g.cost(oracle.AMM)) == (n - 1, 0, (n - 1) ** 2)
     g.order_apply(synth.order_identity(n))  # hub first
-    assert (g.cost(oracle.APP), g.cost(oracle.APM)) == ((n - 1) ** 2, 0)
+    assert (g.cost(oracle.APP), g.cost(oracle.APM), g.cost(oracle.AMM)) == ((n - 1) ** 2, 0, n - 1)
 
 
 @pytest.mark.parametrize("d", [1, 2, 3, 4])
@@ -190,7 +191,7 @@ def test_triangle_free(shape):
     g = oracle.Graph(n, e)
     for rank in (synth.order_identity(n), synth.order_random(n, 3)):
         g.order_apply(rank)
-        for alg in (oracle.APP, oracle.APM):
+        for alg in (oracle.APP, oracle.APM, oracle.AMM):
             for mode in (oracle.LITERAL, oracle.SETS):
                 _, cnt, h, _ = g.list(alg, mode, store=False)
                 assert cnt == 0 and h == 0
@@ -216,7 +217,7 @@ def test_gnp_brute_force(seed):
     g = oracle.Graph(n, e)
     for name, rank in _orderings(n, e):
         g.order_apply(rank)
-        for alg in (oracle.APP, oracle.APM):
+        for alg in (oracle.APP, oracle.APM, oracle.AMM):
             for mode in (oracle.LITERAL, oracle.SETS):
                 t, cnt, h, probes = g.list(alg, mode)
                 assert cnt == len(want), (name, alg, mode)
@@ -230,7 +231,7 @@ def test_k30_brute_force():
     want = set(_pins.brute_force_triangles(n, e))
     assert len(want) == 4060
     g = oracle.Graph(n, e)
-    for alg in (oracle.APP, oracle.APM):
+    for alg in (oracle.APP, oracle.APM, oracle.AMM):
         t, cnt, _, _ = g.list(alg)
         assert _as_set(t) == want
 
@@ -241,7 +242,7 @@ def test_duplicates_loops_and_directions_are_merged():
     noisy = np.concatenate([base, base[:, ::-1], base[:50], np.array([[3, 3], [9, 9]], np.uint32)])
     g0, g1 = oracle.Graph(40, base), oracle.Graph(40, noisy)
     assert g0.m == g1.m == len(_pins.simple_edge_set(base))
-    for alg in (oracle.APP, oracle.APM):
+    for alg in (oracle.APP, oracle.APM, oracle.AMM):
         a = g0.list(alg)
         b = g1.list(alg)
         assert a[1:] == b[1:]
@@ -258,7 +259,7 @@ def test_property1_probes_equal_cost(seed):
     g = oracle.Graph(n, e)
     for name, rank in _orderings(n, e):
         g.order_apply(rank)
-        for alg in (oracle.APP, oracle.APM):
+        for alg in (oracle.APP, oracle.APM, oracle.AMM):
             _, _, _, probes = g.list(alg, oracle.LITERAL, store=False)
             assert probes == g.cost(alg), (name, alg)
 
@@ -287,7 +288,7 @@ def test_invariants_across_orderings_and_algorithms():
             for x in range(0, n, 97):
                 row = adj[off[x]:off[x + 1]]
                 assert np.all(np.diff(row.astype(np.int64)) > 0)
-        for alg in (oracle.APP, oracle.APM):
+        for alg in (oracle.APP, oracle.APM, oracle.AMM):
             t, cnt, h, _ = g.list(alg)
             c = oracle.canonical(t)
             assert len({tuple(r) for r in c.tolist()}) == cnt  # no duplicates
@@ -306,7 +307,7 @@ def test_seed_ranges_partition_the_listing():
     n = 3000
     g = oracle.Graph(n, synth.chung_lu(n, 20, 2.5, 4))
     g.order_apply(synth.order_degree(synth.simple_csr(n, synth.chung_lu(n, 20, 2.5, 4))[0]))
-    for alg in (oracle.APP, oracle.APM):
+    for alg in (oracle.APP, oracle.APM, oracle.AMM):
         _, cnt, h, p = g.list(alg, store=False)
         cuts = [0, 17, 900, 2999, n]
         parts = [g.list(alg, seed_begin=a, seed_end=b, store=False) for a, b in zip(cuts, cuts[1:])]
@@ -422,3 +423,23 @@ def test_core_order_levels_is_a_degeneracy_ordering():
     assert sorted(r[5:].tolist()) == [0, 1, 2] and sorted(r[:5].tolist()) == [3, 4, 5, 6, 7]
     r = oracle.core_order_levels(9, synth.star(9))
     assert r[0] == 8
+
+
+def test_amm_is_app_on_the_reversed_ordering():
+    """A-- (seed edge S2) is the mirror image of A++ (seed edge L): reversing
+    the ordering swaps N+ and N-, so C--(pi) = C++(reversed pi) and both list
+    the same triangles with the same number of tests (the footnote of Sec. 2.1
+    calls their complexities equivalent)."""
+    for seed in range(5):
+        n = 400
+        e = synth.chung_lu(n, 12, 2.3, 90 + seed)
+        g = oracle.Graph(n, e)
+        r = synth.order_random(n, seed)
+        g.order_apply(r)
+        t_mm, c_mm, h_mm, p_mm = g.list(oracle.AMM)
+        cost_mm = g.cost(oracle.AMM)
+        g.order_apply((n - 1 - r.astype(np.int64)).astype(np.uint32))
+        t_pp, c_pp, h_pp, p_pp = g.list(oracle.APP)
+        assert cost_mm == g.cost(oracle.APP) == p_mm == p_pp
+        assert (c_mm, h_mm) == (c_pp, h_pp)
+        assert np.array_equal(oracle.canonical(t_mm), oracle.canonical(t_pp))
