@@ -609,7 +609,7 @@ def ordering_sweep(tl, n, e, e_dev, stream):
     try:
         for name, r in orders.items():
             tl.tl_order_apply(g, torch.from_numpy(r).cuda())
-            for a, an in ((tl.TL_APP, "A++"), (tl.TL_APM, "A+-")):
+            for a, an in ((tl.TL_APP, "A++"), (tl.TL_APM, "A+-"), (tl.TL_AMM, "A--")):
                 ch.reset()
                 tl.tl_list_triangles(g, a, CHUNK_BYTES, tl.tl_count_hash_ptr(), ch.user)
                 st = tl.tl_last_list_stats(g)
@@ -618,7 +618,7 @@ def ordering_sweep(tl, n, e, e_dev, stream):
     finally:
         tl.tl_graph_free(g)
         ch.release()
-    for an in ("A++", "A+-"):
+    for an in ("A++", "A+-", "A--"):
         xs = [r["cost"] for r in rows if r["alg"] == an]
         ys = [r["list_kernel_ms"] for r in rows if r["alg"] == an]
         if len(xs) > 2 and np.std(xs) > 0 and np.std(ys) > 0:

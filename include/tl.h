@@ -62,7 +62,9 @@ typedef enum {
 
 typedef enum {
   TL_APP = 0, /* Algorithm 1, A++ ("L+n"): seed edge L=(u,w), scan N+_u, probe N-_w */
-  TL_APM = 1  /* Algorithm 2, A+- ("S1+n"): seed edge S1=(u,v), scan N+_v, probe N+_u */
+  TL_APM = 1, /* Algorithm 2, A+- ("S1+n"): seed edge S1=(u,v), scan N+_v, probe N+_u */
+  TL_AMM = 2  /* A-- ("S2+n", the third variant of the footnote of Sec. 2.1): seed
+                 edge S2=(v,w), scan N-_w, probe N-_v; work C-- = sum d-_w d-_w */
 } tl_alg;
 
 /* Load an undirected graph.
@@ -152,8 +154,9 @@ TL_EXPORT tl_status tl_order_compute(tl_graph *g, tl_order_kind kind, uint32_t *
                                      int rank_on_device);
 
 /* Cost of the current ordering (Sec. 3.1): TL_APP -> C++ = sum_u d+_u^2,
- * TL_APM -> C+- = sum_u d+_u d-_u.  Exact, uint64.  By Property 1 this is
- * the number of neighbour tests the chosen algorithm performs. */
+ * TL_APM -> C+- = sum_u d+_u d-_u, TL_AMM -> C-- = sum_u d-_u^2.  Exact,
+ * uint64.  By Property 1 (and the same counting for A--) this is the number
+ * of neighbour tests the chosen algorithm performs. */
 TL_EXPORT tl_status tl_cost(const tl_graph *g, tl_alg alg, uint64_t *cost);
 
 /* Consumer of one chunk of triangles.  dev_triples points to n_triples
@@ -170,7 +173,9 @@ typedef int (*tl_consumer)(const uint32_t *dev_triples, uint64_t n_triples,
  *   TL_APP: for each oriented edge (u, w), every v in N+_u that is in N-_w
  *           gives triangle {u, v, w} (Algorithm 1);
  *   TL_APM: for each oriented edge (u, v), every w in N+_v that is in N+_u
- *           gives triangle {u, v, w} (Algorithm 2).
+ *           gives triangle {u, v, w} (Algorithm 2);
+ *   TL_AMM: for each oriented edge (v, w), every u in N-_w that is in N-_v
+ *           gives triangle {u, v, w} (A--).
  * Triangles are reported in original ids, sorted, in chunks of at most
  * chunk_bytes / 12 triples (chunk_bytes >= TL_MIN_CHUNK_BYTES; two chunk
  * buffers are allocated per call).  cb may be NULL (triangles are then only
@@ -181,7 +186,8 @@ TL_EXPORT tl_status tl_list_triangles(tl_graph *g, tl_alg alg, size_t chunk_byte
                             tl_consumer cb, void *user, uint64_t *n_triangles);
 
 /* Same, restricted to the seed vertices of rank [x_begin, x_end): the
- * vertex w of Algorithm 1's outer loop (A++) or u of Algorithm 2's (A+-).
+ * vertex w of Algorithm 1's outer loop (A++), u of Algorithm 2's (A+-) or v
+ * of A--'s.
  * Disjoint ranges list disjoint triangle sets whose union over a partition
  * of [0, n) is the full set; this is how independent replicas split one
  * graph.  Also returns the number of neighbour tests performed in
@@ -268,13 +274,13 @@ TL_EXPORT int tl_count_hash_noalloc(const uint32_t *dev_triples, uint64_t n_trip
  * The paper has no counterpart (it lists one graph at a time); this is the
  * request loop around the same path.  Graphs and their orderings are
  * registered once and stay on the device.  A request names a registered
- * graph, one of its registered orderings and an algorithm (TL_APP or
- * TL_APM), and gets back the count and set hash H (as tl_count_hash) of the
+ * graph, one of its registered orderings and an algorithm (TL_APP, TL_APM
+ * or TL_AMM), and gets back the count and set hash H (as tl_count_hash) of the
  * graph's triangles.  Worker threads, one CUDA stream each, form batches:
  * a worker takes the oldest waiting requests, as many as fit (at most
  * max_batch, their estimated device footprint within what the budget has
- * left), lists them as one disjoint union (tl_graph_union: A++ requests
- * over the first rank range, A+- requests over the rest) and completes them
+ * left), lists them as one disjoint union (tl_graph_union; the requests
+ * grouped by algorithm, one listing range per group) and completes them
  * together.  With workers >= 2, requests that arrive while one batch is on
  * the GPU are admitted into the next as soon as a worker and memory are
  * free, and the two batches overlap on the device.  max_batch = 1 serves

@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtl.so")
 
 TL_OK, TL_EINVAL, TL_ENOMEM, TL_ECUDA, TL_ESTATE, TL_ECALLBACK, TL_ETIMEOUT = range(7)
-TL_APP, TL_APM = 0, 1
+TL_APP, TL_APM, TL_AMM = 0, 1, 2
 TL_MIN_CHUNK_BYTES = 12 << 20
 STATUS_NAMES = {0: "TL_OK", 1: "TL_EINVAL", 2: "TL_ENOMEM", 3: "TL_ECUDA", 4: "TL_ESTATE",
                 5: "TL_ECALLBACK", 6: "TL_ETIMEOUT"}

@@ -123,17 +123,33 @@ void require_device() {
                            (e != cudaSuccess ? cudaGetErrorString(e) : "device count is 0"));
 }
 
+// The three CSR roles of one algorithm (Sec. 2.1): the probe set P_x put in
+// B, the seeds y of x, and the list scanned for each seed.
+//   A++ (seed edge L):  P_x = N-_x, seeds N-_x, scan N+_y
+//   A+- (seed edge S1): P_x = N+_x, seeds N+_x, scan N+_y
+//   A-- (seed edge S2): P_x = N-_x, seeds N+_x, scan N-_y
+struct Sides {
+  const uint64_t *poff, *soff, *scan_off;
+  const uint32_t *padj, *sadj, *scan_adj;
+};
+Sides sides(const tl::DeviceGraph &g, int alg) {
+  const uint64_t *io = g.in_off.as<uint64_t>(), *oo = g.out_off.as<uint64_t>();
+  const uint32_t *ia = g.in_adj.as<uint32_t>(), *oa = g.out_adj.as<uint32_t>();
+  if (alg == TL_APP) return Sides{io, io, oo, ia, ia, oa};
+  if (alg == TL_APM) return Sides{oo, oo, oo, oa, oa, oa};
+  return Sides{io, oo, io, ia, oa, ia};
+}
+
 // a6: per-seed-edge work prefix and the task counts of both kernels.
 void bucketize(tl_graph *G, int alg, uint32_t xb, uint32_t xe) {
   if (G->cached_alg == alg && G->cached_xb == xb && G->cached_xe == xe) return;
   tl::DeviceGraph &g = G->g;
   cudaStream_t s = g.stream;
   const uint64_t m = g.m;
-  const uint64_t *poff = (alg == TL_APP) ? g.in_off.as<uint64_t>() : g.out_off.as<uint64_t>();
-  const uint32_t *padj = (alg == TL_APP) ? g.in_adj.as<uint32_t>() : g.out_adj.as<uint32_t>();
+  const Sides sd = sides(g, alg);
   G->wseed.reserve((m ? m : 1) * 4);
   G->WP.reserve((m + 1) * 8);
-  if (m) tl::launch_seed_work(padj, m, g.out_off.as<uint64_t>(), G->wseed.as<uint32_t>(), s);
+  if (m) tl::launch_seed_work(sd.sadj, m, sd.scan_off, G->wseed.as<uint32_t>(), s);
   tl::exclusive_scan_u32_to_u64(G->wseed.as<uint32_t>(), G->WP.as<uint64_t>(), m, g.scan_tmp, s);
   const uint64_t nr = xe - xb;
   const uint64_t nr1 = nr ? nr : 1;
@@ -150,7 +166,7 @@ void bucketize(tl_graph *G, int alg, uint32_t xb, uint32_t xe) {
     G->piece_prefix[t].reserve((nr + 1) * 8);
   }
   if (nr)
-    tl::launch_classify(poff, G->WP.as<uint64_t>(), xb, xe, G->tw[0].as<uint64_t>(),
+    tl::launch_classify(sd.poff, sd.soff, G->WP.as<uint64_t>(), xb, xe, G->tw[0].as<uint64_t>(),
                         G->tw[1].as<uint64_t>(), G->tf[0].as<uint32_t>(), G->tf[1].as<uint32_t>(),
                         G->pieces[0].as<uint64_t>(), G->pieces[1].as<uint64_t>(), s);
   for (int t = 0; t < 2; ++t) {
@@ -205,7 +221,8 @@ tl_status list_impl(tl_graph *G, int alg, uint32_t xb, uint32_t xe, size_t chunk
                     tl_consumer cb, void *user, uint64_t *n_triangles, uint64_t *n_probes) {
   TL_API_BEGIN
   if (!G) tl::fail(TL_EINVAL, "graph is NULL");
-  if (alg != TL_APP && alg != TL_APM) tl::fail(TL_EINVAL, "alg must be TL_APP or TL_APM");
+  if (alg != TL_APP && alg != TL_APM && alg != TL_AMM)
+    tl::fail(TL_EINVAL, "alg must be TL_APP, TL_APM or TL_AMM");
   tl::DeviceGraph &g = G->g;
   ensure_ordered(G);
   if (xb > xe || xe > g.n) tl::fail(TL_EINVAL, "seed range outside [0, n]");
@@ -255,10 +272,13 @@ tl_status list_impl(tl_graph *G, int alg, uint32_t xb, uint32_t xe, size_t chunk
   a.n = g.n;
   a.x_begin = xb;
   a.x_end = xe;
-  a.poff = (alg == TL_APP) ? g.in_off.as<uint64_t>() : g.out_off.as<uint64_t>();
-  a.padj = (alg == TL_APP) ? g.in_adj.as<uint32_t>() : g.out_adj.as<uint32_t>();
-  a.out_off = g.out_off.as<uint64_t>();
-  a.out_adj = g.out_adj.as<uint32_t>();
+  const Sides sd = sides(g, alg);
+  a.poff = sd.poff;
+  a.padj = sd.padj;
+  a.soff = sd.soff;
+  a.sadj = sd.sadj;
+  a.scan_off = sd.scan_off;
+  a.scan_adj = sd.scan_adj;
   a.inv = g.inv.as<uint32_t>();
   a.WP = G->WP.as<uint64_t>();
   a.ctl = G->ctl.as<tl::ListCtl>();
@@ -493,9 +513,10 @@ tl_status tl_order_compute(tl_graph *G, tl_order_kind kind, uint32_t *rank, int 
 tl_status tl_cost(const tl_graph *G, tl_alg alg, uint64_t *cost) {
   TL_API_BEGIN
   if (!G || !cost) tl::fail(TL_EINVAL, "graph or cost is NULL");
-  if (alg != TL_APP && alg != TL_APM) tl::fail(TL_EINVAL, "alg must be TL_APP or TL_APM");
+  if (alg != TL_APP && alg != TL_APM && alg != TL_AMM)
+    tl::fail(TL_EINVAL, "alg must be TL_APP, TL_APM or TL_AMM");
   ensure_ordered(const_cast<tl_graph *>(G));
-  *cost = (alg == TL_APP) ? G->g.cost_app : G->g.cost_apm;
+  *cost = alg == TL_APP ? G->g.cost_app : (alg == TL_APM ? G->g.cost_apm : G->g.cost_amm);
   TL_API_END
 }
 

@@ -125,16 +125,18 @@ __global__ void k_offsets(const uint64_t *__restrict__ keys, uint64_t m, uint32_
 }
 
 // acc[0] += sum d+^2 (C++), acc[1] += sum d+ d- (C+-), acc[2] = max d+,
-// acc[3] = max d- (Definition of Sec. 3.1).
+// acc[3] = max d- (Definition of Sec. 3.1), acc[4] += sum d-^2 (C--, the
+// cost of A--).
 __global__ void k_cost(const uint64_t *__restrict__ out_off, const uint64_t *__restrict__ in_off,
                        uint32_t n, unsigned long long *__restrict__ acc) {
-  unsigned long long s_pp = 0, s_pm = 0, mx_p = 0, mx_m = 0;
+  unsigned long long s_pp = 0, s_pm = 0, s_mm = 0, mx_p = 0, mx_m = 0;
   for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < n;
        x += (uint64_t)gridDim.x * blockDim.x) {
     unsigned long long dp = out_off[x + 1] - out_off[x];
     unsigned long long dm = in_off[x + 1] - in_off[x];
     s_pp += dp * dp;
     s_pm += dp * dm;
+    s_mm += dm * dm;
     mx_p = dp > mx_p ? dp : mx_p;
     mx_m = dm > mx_m ? dm : mx_m;
   }
@@ -142,6 +144,7 @@ __global__ void k_cost(const uint64_t *__restrict__ out_off, const uint64_t *__r
   for (int d = 16; d > 0; d >>= 1) {
     s_pp += __shfl_down_sync(0xffffffffu, s_pp, d);
     s_pm += __shfl_down_sync(0xffffffffu, s_pm, d);
+    s_mm += __shfl_down_sync(0xffffffffu, s_mm, d);
     unsigned long long a = __shfl_down_sync(0xffffffffu, mx_p, d);
     unsigned long long b = __shfl_down_sync(0xffffffffu, mx_m, d);
     mx_p = a > mx_p ? a : mx_p;
@@ -152,6 +155,7 @@ __global__ void k_cost(const uint64_t *__restrict__ out_off, const uint64_t *__r
     atomicAdd(&acc[1], s_pm);
     atomicMax(&acc[2], mx_p);
     atomicMax(&acc[3], mx_m);
+    atomicAdd(&acc[4], s_mm);
   }
 }
 
@@ -358,7 +362,7 @@ void build_dag(DeviceGraph &g, const uint32_t *rank, bool on_device) {
   // +4 elements: the listing kernels read N+ lists with aligned 16-byte loads
   // that may extend up to 3 elements past the last list.
   g.out_adj.reserve((m + 4) * 4);
-  g.in_adj.reserve((m ? m : 1) * 4);
+  g.in_adj.reserve((m + 4) * 4);  // scanned by A-- with the same 16-byte loads
   if (m > 0) {
     // a3: relabel + orient.
     g.keys_a.reserve(m * 8);
@@ -391,11 +395,12 @@ void build_dag(DeviceGraph &g, const uint32_t *rank, bool on_device) {
   k_cost<<<grid_for(n, kThreads), kThreads, 0, s>>>(g.out_off.as<uint64_t>(),
                                                     g.in_off.as<uint64_t>(), n, acc);
   TL_CHECK_LAUNCH();
-  unsigned long long h[4];
+  unsigned long long h[5];
   TL_CUDA(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, s));
   TL_CUDA(cudaStreamSynchronize(s));
   g.cost_app = h[0];
   g.cost_apm = h[1];
+  g.cost_amm = h[4];
   g.max_out_deg = (uint32_t)h[2];
   g.max_in_deg = (uint32_t)h[3];
   g.ordered = true;

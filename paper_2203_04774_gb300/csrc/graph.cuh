@@ -20,7 +20,7 @@ struct DeviceGraph {
   DevBuf E, rank, inv, out_off, out_adj, in_off, in_adj;
   // workspaces (kept between calls so repeated calls do not reallocate)
   DevBuf keys_a, keys_b, sort_tmp, scan_tmp, small;  // small: flags/counters
-  uint64_t cost_app = 0, cost_apm = 0;
+  uint64_t cost_app = 0, cost_apm = 0, cost_amm = 0;
   uint32_t max_out_deg = 0, max_in_deg = 0;
   // A disjoint union's part table: part i holds vertices [vbase[i], vbase[i+1]);
   // empty for a graph loaded whole.

@@ -288,10 +288,9 @@ __device__ __forceinline__ bool fetch_piece(const ListArgs &a, uint32_t &x, uint
   if (t >= a.n_tasks) return false;
   x = a.task_x[t];
   const uint64_t piece = t - a.piece_prefix[x - a.x_begin];
-  const uint64_t pb = a.poff[x], pe = a.poff[x + 1];
-  const uint64_t w1 = a.WP[pe];
-  const uint64_t pw = piece_work(a.tier, pe - pb);
-  ia = a.WP[pb] + piece * pw;
+  const uint64_t w1 = a.WP[a.soff[x + 1]];
+  const uint64_t pw = piece_work(a.tier, a.poff[x + 1] - a.poff[x]);
+  ia = a.WP[a.soff[x]] + piece * pw;
   ib = ia + pw < w1 ? ia + pw : w1;
   return true;
 }
@@ -325,9 +324,9 @@ __device__ void commit_warp(ListCtl *ctl, const ListArgs &a, int64_t t, const ui
   __syncwarp();
 }
 
-// Warp-level walk of the tests [i0, i1) of B vertex x, whose probe-side row
-// is [pb, pe); k0 is the seed edge holding test i0 (found by binary search
-// when ~0).  For each test: z = the scanned element, member(z) = B[z].  Hits
+// Warp-level walk of the tests [i0, i1) of B vertex x, whose seed row is
+// [pb, pe) (entries of sadj); k0 is the seed edge holding test i0 (found by
+// binary search when ~0).  For each test: z = the scanned element, member(z) = B[z].  Hits
 // go to the warp's own global slab as (original id of x, original id of y,
 // rank of z) at positions counted by wcnt (kEmit 0, warp tiers), or to the
 // warp's shared-memory buffer as (original id of y, rank of z), flushed to the
@@ -355,8 +354,8 @@ __device__ __forceinline__ void scan_items(const ListArgs &a, uint64_t pb, uint6
     if (valid) {
       B = a.WP[kk];
       E = a.WP[kk + 1];
-      const uint32_t y = a.padj[kk];
-      A = a.out_off[y] - B;  // scanned element of test i is out_adj[A + i]
+      const uint32_t y = a.sadj[kk];
+      A = a.scan_off[y] - B;  // scanned element of test i is scan_adj[A + i]
       iy = a.inv[y];
     }
     Elast = shfl_u64(E, 31);
@@ -401,7 +400,7 @@ __device__ __forceinline__ void scan_items(const ListArgs &a, uint64_t pb, uint6
       const uint32_t iyj = __shfl_sync(0xffffffffu, iy, j0);
       const uint64_t run = (Ej0 < i1 ? Ej0 : i1) - base;
       // Each lane takes 4 consecutive elements with one aligned 16-byte load
-      // (out_adj is 256-byte aligned and padded by 4 elements; elements
+      // (scan_adj is 256-byte aligned and padded by 4 elements; elements
       // outside [lo, hi) are masked), and the warp reserves slab room for the
       // 128 tests of an iteration at once.
       const uint64_t lo = Aj, hi = Aj + run;
@@ -412,7 +411,7 @@ __device__ __forceinline__ void scan_items(const ListArgs &a, uint64_t pb, uint6
         }
         const uint64_t q = q0 + 4 * lane;
         uint4 v = make_uint4(0, 0, 0, 0);
-        if (q < hi) v = *reinterpret_cast<const uint4 *>(a.out_adj + q);
+        if (q < hi) v = *reinterpret_cast<const uint4 *>(a.scan_adj + q);
         const uint32_t z[4] = {v.x, v.y, v.z, v.w};
         // the iteration's tests: [max(q0, lo), min(q0 + 128, hi)), counted once
         if (lane == 0) probes += (q0 + 128 < hi ? q0 + 128 : hi) - (q0 > lo ? q0 : lo);
@@ -473,7 +472,7 @@ __device__ __forceinline__ void scan_items(const ListArgs &a, uint64_t pb, uint6
     bool hit = false;
     uint32_t z = 0;
     if (act) {
-      z = a.out_adj[Aj + base + off];
+      z = a.scan_adj[Aj + base + off];
       ++probes;
       hit = member(z);
     }
@@ -503,6 +502,7 @@ __global__ void __launch_bounds__(kWarpThreads, 4) k_list_warp(ListArgs a) {
     for (uint32_t idx = i0; idx < i1; ++idx) {
       const uint32_t x = a.tier_x[idx];
       const uint64_t pb = a.poff[x], pe = a.poff[x + 1];
+      const uint64_t sb = a.soff[x], se = a.soff[x + 1];
       const uint32_t p = (uint32_t)(pe - pb);
       int lg = 6;
       while ((1u << lg) < 2 * p) ++lg;  // 2p <= SLOTS by the tier's definition
@@ -511,7 +511,7 @@ __global__ void __launch_bounds__(kWarpThreads, 4) k_list_warp(ListArgs a) {
       __syncwarp();
       for (uint64_t q = pb + lane; q < pe; q += 32) hash_insert(H, lg, a.padj[q]);
       __syncwarp();
-      scan_items<0>(a, pb, pe, pb, a.WP[pb], a.WP[pe], a.inv[x],
+      scan_items<0>(a, sb, se, sb, a.WP[sb], a.WP[se], a.inv[x],
                     [&](uint32_t z) { return hash_find(H, lg, z); }, slab, nout, cnt, probes);
       __syncwarp();
     }
@@ -599,7 +599,8 @@ __global__ void __launch_bounds__(THREADS, TIER == 3 ? 1 : 4) k_list_cta(ListArg
     __syncthreads();
     if (!s_ok) break;
     const uint32_t x = s_x;
-    const uint64_t pb = a.poff[x], pe = a.poff[x + 1];
+    const uint64_t pb = a.poff[x], pe = a.poff[x + 1];  // probe set P_x
+    const uint64_t sb = a.soff[x], se = a.soff[x + 1];  // seeds
     const uint32_t mode = s_mode;
     const int lg = (int)s_lg;
     const uint64_t wa = s_rng[wid][0], wb = s_rng[wid][1];  // this warp's tests
@@ -634,16 +635,16 @@ __global__ void __launch_bounds__(THREADS, TIER == 3 ? 1 : 4) k_list_cta(ListArg
     o.probes_safe = 0;
     o.failed = false;
     if (mode == 0) {
-      scan_items<1>(a, pb, pe, ~0ull, wa, wb, inv_x,
+      scan_items<1>(a, sb, se, ~0ull, wa, wb, inv_x,
                     [&](uint32_t z) { return ((sm[z >> 5] >> (z & 31)) & 1u) != 0; }, nullptr,
                     o, unused, probes);
     } else if (mode == 1) {
-      scan_items<1>(a, pb, pe, ~0ull, wa, wb, inv_x,
+      scan_items<1>(a, sb, se, ~0ull, wa, wb, inv_x,
                     [&](uint32_t z) { return bucket_find(sm, lg - 2, z); }, nullptr, o, unused,
                     probes);
     } else if (mode == 3) {
       const uint32_t *gh = a.ghash + (uint64_t)blockIdx.x * kGHashSlots;
-      scan_items<1>(a, pb, pe, ~0ull, wa, wb, inv_x,
+      scan_items<1>(a, sb, se, ~0ull, wa, wb, inv_x,
                     [&](uint32_t z) {
                       const uint32_t f = fslot(z);
                       if (((sm[f >> 5] >> (f & 31)) & 1u) == 0) return false;
@@ -651,7 +652,7 @@ __global__ void __launch_bounds__(THREADS, TIER == 3 ? 1 : 4) k_list_cta(ListArg
                     },
                     nullptr, o, unused, probes);
     } else {
-      scan_items<1>(a, pb, pe, ~0ull, wa, wb, inv_x,
+      scan_items<1>(a, sb, se, ~0ull, wa, wb, inv_x,
                     [&](uint32_t z) {
                       uint64_t lo = pb, hi = pe;
                       while (lo < hi) {
@@ -701,17 +702,18 @@ __global__ void __launch_bounds__(THREADS, TIER == 3 ? 1 : 4) k_list_cta(ListArg
 
 // ---- bucketize (a6) -----------------------------------------------------------
 
-// w[k] = d+(y_k) for every probe-side CSR entry k.
-__global__ void k_seed_work(const uint32_t *__restrict__ padj, uint64_t m,
-                            const uint64_t *__restrict__ out_off, uint32_t *__restrict__ w) {
+// w[k] = length of the list scanned for seed entry k (d+ of y_k, or d- for A--).
+__global__ void k_seed_work(const uint32_t *__restrict__ sadj, uint64_t m,
+                            const uint64_t *__restrict__ scan_off, uint32_t *__restrict__ w) {
   for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < m;
        k += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t y = padj[k];
-    w[k] = (uint32_t)(out_off[y + 1] - out_off[y]);
+    const uint32_t y = sadj[k];
+    w[k] = (uint32_t)(scan_off[y + 1] - scan_off[y]);
   }
 }
 
-__global__ void k_classify(const uint64_t *__restrict__ poff, const uint64_t *__restrict__ WP,
+__global__ void k_classify(const uint64_t *__restrict__ poff, const uint64_t *__restrict__ soff,
+                           const uint64_t *__restrict__ WP,
                            uint32_t x_begin, uint32_t x_end, uint64_t *__restrict__ w0,
                            uint64_t *__restrict__ w1, uint32_t *__restrict__ f0,
                            uint32_t *__restrict__ f1, uint64_t *__restrict__ pieces2,
@@ -720,11 +722,12 @@ __global__ void k_classify(const uint64_t *__restrict__ poff, const uint64_t *__
   for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < nr;
        r += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t x = x_begin + (uint32_t)r;
-    const uint64_t pb = poff[x], pe = poff[x + 1];
-    const uint64_t W = WP[pe] - WP[pb];
-    const uint64_t p = pe - pb;
+    const uint64_t W = WP[soff[x + 1]] - WP[soff[x]];
+    const uint64_t p = poff[x + 1] - poff[x];
     uint64_t a0 = 0, a1 = 0, n2 = 0, n3 = 0;
-    if (p > 0 && W > 0) {
+    // every prescribed test runs, also when P_x is empty (possible for A--,
+    // whose seeds are not its probe set): the work then equals the cost
+    if (W > 0) {
       if (p <= kSmallMaxP && W <= kWarpWork)
         a0 = W + kVertexCost;
       else if (p <= kMediumMaxP && W <= kWarpWork)
@@ -871,17 +874,18 @@ constexpr int kSmemMid = kMidSmemBytes;
 
 // ---- host side ----------------------------------------------------------------
 
-void launch_seed_work(const uint32_t *padj, uint64_t m, const uint64_t *out_off, uint32_t *w,
+void launch_seed_work(const uint32_t *sadj, uint64_t m, const uint64_t *scan_off, uint32_t *w,
                       cudaStream_t s) {
-  k_seed_work<<<grid_for(m, 256), 256, 0, s>>>(padj, m, out_off, w);
+  k_seed_work<<<grid_for(m, 256), 256, 0, s>>>(sadj, m, scan_off, w);
   TL_CHECK_LAUNCH();
 }
 
-void launch_classify(const uint64_t *poff, const uint64_t *WP, uint32_t x_begin, uint32_t x_end,
+void launch_classify(const uint64_t *poff, const uint64_t *soff, const uint64_t *WP,
+                     uint32_t x_begin, uint32_t x_end,
                      uint64_t *w0, uint64_t *w1, uint32_t *f0, uint32_t *f1, uint64_t *pieces2,
                      uint64_t *pieces3, cudaStream_t s) {
   k_classify<<<grid_for((uint64_t)(x_end - x_begin), 256), 256, 0, s>>>(
-      poff, WP, x_begin, x_end, w0, w1, f0, f1, pieces2, pieces3);
+      poff, soff, WP, x_begin, x_end, w0, w1, f0, f1, pieces2, pieces3);
   TL_CHECK_LAUNCH();
 }
 

@@ -85,12 +85,18 @@ struct RetryPiece {
 
 struct ListArgs {
   uint32_t n, x_begin, x_end;
-  const uint64_t *poff;          // probe-side CSR: A++ -> N-, A+- -> N+
+  // For B vertex x: probe set P_x = padj[poff[x], poff[x+1]); seeds y =
+  // sadj[soff[x], soff[x+1]); for each seed, the list scan_adj[scan_off[y],
+  // scan_off[y+1]) is scanned.  A++: N-, N-, N+;  A+-: N+, N+, N+;
+  // A--: N-, N+, N-.
+  const uint64_t *poff;
   const uint32_t *padj;
-  const uint64_t *out_off;       // scanned lists N+
-  const uint32_t *out_adj;
+  const uint64_t *soff;
+  const uint32_t *sadj;
+  const uint64_t *scan_off;
+  const uint32_t *scan_adj;      // read 16 bytes at a time: padded by 4 elements
   const uint32_t *inv;           // rank -> original id
-  const uint64_t *WP;            // work prefix over probe-side entries [m+1]
+  const uint64_t *WP;            // work prefix over seed-side entries [m+1]
   // warp tiers: the tier's vertices in rank order and their work prefix
   // [count+1]; task t holds vertices [task_start[t], task_start[t+1])
   const uint32_t *tier_x;
@@ -117,11 +123,12 @@ struct ListArgs {
   uint64_t n_tasks;
 };
 
-void launch_seed_work(const uint32_t *padj, uint64_t m, const uint64_t *out_off, uint32_t *w,
+void launch_seed_work(const uint32_t *sadj, uint64_t m, const uint64_t *scan_off, uint32_t *w,
                       cudaStream_t s);
 // Per x in [x_begin, x_end): weight in tier 0 / 1 (0 if not in the tier),
 // the membership flags, and the piece counts of tiers 2 and 3.
-void launch_classify(const uint64_t *poff, const uint64_t *WP, uint32_t x_begin, uint32_t x_end,
+void launch_classify(const uint64_t *poff, const uint64_t *soff, const uint64_t *WP,
+                     uint32_t x_begin, uint32_t x_end,
                      uint64_t *w0, uint64_t *w1, uint32_t *f0, uint32_t *f1, uint64_t *pieces2,
                      uint64_t *pieces3, cudaStream_t s);
 // Compact the vertices of one warp tier: x_list[pos[r]] = x, wp_list[pos[r]] = pref[r].

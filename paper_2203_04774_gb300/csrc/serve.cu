@@ -80,12 +80,10 @@ void run_batch(tl_server *S, Worker &W, std::vector<Request *> &batch) {
   std::vector<const tl_graph *> parts(k);
   std::vector<const uint32_t *> ranks(k);
   std::vector<uint64_t> vb(k + 1, 0);
-  uint32_t n_app = 0;
   for (uint32_t i = 0; i < k; ++i) {
     parts[i] = batch[i]->g;
     ranks[i] = batch[i]->rank;
     vb[i + 1] = vb[i] + batch[i]->n;
-    n_app += batch[i]->alg == TL_APP;
   }
   tl_status st = TL_OK;
   std::vector<uint64_t> counts(k, 0), hashes(k, 0);
@@ -100,13 +98,15 @@ void run_batch(tl_server *S, Worker &W, std::vector<Request *> &batch) {
               cudaMemsetAsync(W.d_hashes, 0, k * 8, W.cstream) == cudaSuccess &&
               cudaStreamSynchronize(W.cstream) == cudaSuccess;
     if (!ok) st = TL_ECUDA;
-    const uint32_t split = (uint32_t)vb[n_app];
-    if (st == TL_OK && n_app > 0)
-      st = tl_list_triangles_range(u, TL_APP, 0, split, S->cfg.chunk_bytes, tl_count_hash_parts,
-                                   &cs, nullptr, nullptr);
-    if (st == TL_OK && n_app < k)
-      st = tl_list_triangles_range(u, TL_APM, split, (uint32_t)vb[k], S->cfg.chunk_bytes,
-                                   tl_count_hash_parts, &cs, nullptr, nullptr);
+    // one listing range per run of requests with the same algorithm
+    for (uint32_t i = 0; st == TL_OK && i < k;) {
+      uint32_t j = i;
+      while (j < k && batch[j]->alg == batch[i]->alg) ++j;
+      st = tl_list_triangles_range(u, batch[i]->alg, (uint32_t)vb[i], (uint32_t)vb[j],
+                                   S->cfg.chunk_bytes, tl_count_hash_parts, &cs, nullptr,
+                                   nullptr);
+      i = j;
+    }
     if (st == TL_OK) {
       ok = cudaMemcpyAsync(counts.data(), W.d_counts, k * 8, cudaMemcpyDeviceToHost,
                            W.cstream) == cudaSuccess &&
@@ -312,7 +312,8 @@ tl_status tl_server_submit(tl_server *S, uint32_t graph_id, uint32_t ordering_id
                            uint64_t *request_id) {
   TL_SERVE_BEGIN
   if (!S || !request_id) tl::fail(TL_EINVAL, "NULL argument");
-  if (alg != TL_APP && alg != TL_APM) tl::fail(TL_EINVAL, "alg must be TL_APP or TL_APM");
+  if (alg != TL_APP && alg != TL_APM && alg != TL_AMM)
+    tl::fail(TL_EINVAL, "alg must be TL_APP, TL_APM or TL_AMM");
   Request *r = new Request();
   r->res.t_submit_ns = now_ns();
   {

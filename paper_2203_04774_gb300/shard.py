@@ -11,18 +11,21 @@ from __future__ import annotations
 
 import numpy as np
 
-TL_APP, TL_APM = 0, 1
+TL_APP, TL_APM, TL_AMM = 0, 1, 2
 
 
 def seed_work(out_off: np.ndarray, out_adj: np.ndarray, in_off: np.ndarray, in_adj: np.ndarray,
               alg: int) -> np.ndarray:
     """Membership tests of each seed rank x (Property 1, per vertex):
     A++ (x = w): sum of d+_u over u in N-_w; A+- (x = u): sum of d+_v over v
-    in N+_u.  Inputs are the rank-space CSR of N+ and N- (``tl_graph_csr``)."""
+    in N+_u; A-- (x = v): sum of d-_w over w in N+_v.  Inputs are the
+    rank-space CSR of N+ and N- (``tl_graph_csr``)."""
     dplus = np.diff(np.asarray(out_off, dtype=np.int64))
+    dminus = np.diff(np.asarray(in_off, dtype=np.int64))
     off, adj = (in_off, in_adj) if alg == TL_APP else (out_off, out_adj)
+    length = dminus if alg == TL_AMM else dplus
     off = np.asarray(off, dtype=np.int64)
-    vals = dplus[np.asarray(adj, dtype=np.int64)]
+    vals = length[np.asarray(adj, dtype=np.int64)]
     csum = np.zeros(len(vals) + 1, dtype=np.int64)
     np.cumsum(vals, out=csum[1:])
     return csum[off[1:]] - csum[off[:-1]]

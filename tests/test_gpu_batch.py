@@ -77,7 +77,7 @@ def _check_union(u, parts, ranks, algs_by_part, chunk_bytes=tl.TL_MIN_CHUNK_BYTE
         ref = oracle.Graph(n, e)
         ref.order_apply(r)
         refs.append(ref)
-    for alg in (tl.TL_APP, tl.TL_APM):
+    for alg in (tl.TL_APP, tl.TL_APM, tl.TL_AMM):
         assert u.cost(alg) == sum(ref.cost(alg) for ref in refs)
     # runs of consecutive parts with the same algorithm -> one range call each
     runs, i = [], 0
@@ -121,7 +121,7 @@ def test_load_parts_identity_and_degree_orderings():
     assert u.n == sum(sizes)
     assert u.m == sum(oracle.Graph(n, e).m for n, e in parts)
     ident = [synth.order_identity(n) for n in sizes]
-    for alg in (tl.TL_APP, tl.TL_APM):
+    for alg in (tl.TL_APP, tl.TL_APM, tl.TL_AMM):
         _check_union(u, parts, ident, [alg] * len(parts))
     # device orderings of a union are computed part by part
     vb = _vbase(sizes)
@@ -245,7 +245,7 @@ def test_union_many_parts_every_tier():
     vb = _vbase(sizes)
     rank_np = rank_u.cpu().numpy().astype(np.int64)
     seen = np.zeros(4, np.int64)
-    for alg in (tl.TL_APP, tl.TL_APM):
+    for alg in (tl.TL_APP, tl.TL_APM, tl.TL_AMM):
         nt, c, h, probes = u.list_count_hash_parts(alg, sizes)
         seen += np.array(tl.tl_last_list_stats(u.h)["tasks"]) > 0
         tot_probes = 0

@@ -41,7 +41,7 @@ def _orderings(n, e, which=("identity", "random", "degree", "core", "split", "ch
         yield name, table[name]()
 
 
-def _compare(n, e, orderings, algs=(tl.TL_APP, tl.TL_APM), chunk_bytes=tl.TL_MIN_CHUNK_BYTES,
+def _compare(n, e, orderings, algs=(tl.TL_APP, tl.TL_APM, tl.TL_AMM), chunk_bytes=tl.TL_MIN_CHUNK_BYTES,
              host_edges=False):
     g = tl.Graph(n, e if host_edges else _dev(e))
     ref = oracle.Graph(n, e)
@@ -92,10 +92,11 @@ def test_complete_graphs(n):
     g = tl.Graph(n, _dev(e))
     for rank in (synth.order_identity(n), synth.order_random(n, 3)):
         g.order_apply(_dev(rank))
-        assert (g.cost(tl.TL_APP), g.cost(tl.TL_APM)) == (cpp, cpm)
-        for alg in (tl.TL_APP, tl.TL_APM):
+        # C-- of K_n equals C++ (d-_v = rank of v, mirrored)
+        assert (g.cost(tl.TL_APP), g.cost(tl.TL_APM), g.cost(tl.TL_AMM)) == (cpp, cpm, cpp)
+        for alg in (tl.TL_APP, tl.TL_APM, tl.TL_AMM):
             t, nt, probes, _ = g.list_collect(alg)
-            assert nt == tri and probes == (cpp if alg == tl.TL_APP else cpm)
+            assert nt == tri and probes == (cpm if alg == tl.TL_APM else cpp)
             assert len(set(map(tuple, t.tolist()))) == tri
 
 
@@ -137,7 +138,7 @@ def test_host_edges_and_host_rank():
     g.order_apply(rank)  # host pointer
     ref = oracle.Graph(n, e)
     ref.order_apply(rank)
-    for alg in (tl.TL_APP, tl.TL_APM):
+    for alg in (tl.TL_APP, tl.TL_APM, tl.TL_AMM):
         t, nt, _, _ = g.list_collect(alg)
         assert np.array_equal(oracle.canonical(t), oracle.canonical(ref.list(alg)[0]))
 
@@ -156,7 +157,7 @@ def test_edge_cases_empty_and_tiny():
                  (3, np.array([[1, 1], [2, 2]], np.uint32)), (2, np.array([[0, 1]], np.uint32)),
                  (3, np.array([[0, 1], [1, 2], [2, 0]], np.uint32))]:
         g = tl.Graph(n, e)
-        for alg in (tl.TL_APP, tl.TL_APM):
+        for alg in (tl.TL_APP, tl.TL_APM, tl.TL_AMM):
             t, nt, probes, calls = g.list_collect(alg)
             want = len(_pins.brute_force_triangles(n, e))
             assert nt == want == len(t)
@@ -191,7 +192,7 @@ def test_many_chunks_k300():
     e = synth.complete(n)
     g = tl.Graph(n, _dev(e))
     g.order_apply(_dev(synth.order_random(n, 5)))
-    for alg in (tl.TL_APP, tl.TL_APM):
+    for alg in (tl.TL_APP, tl.TL_APM, tl.TL_AMM):
         t, nt, probes, calls = g.list_collect(alg, tl.TL_MIN_CHUNK_BYTES)
         assert nt == len(t) == 300 * 299 * 298 // 6
         assert calls >= 5
@@ -208,7 +209,7 @@ def test_seed_ranges_partition():
     g.order_apply(_dev(rank))
     ref = oracle.Graph(n, e)
     ref.order_apply(rank)
-    for alg in (tl.TL_APP, tl.TL_APM):
+    for alg in (tl.TL_APP, tl.TL_APM, tl.TL_AMM):
         cuts = [0, 1, 777, 5000, 9990, n]
         parts = []
         for a, b in zip(cuts, cuts[1:]):
@@ -230,7 +231,7 @@ def test_count_hash_consumer_matches_oracle():
     g.order_apply(_dev(rank))
     ref = oracle.Graph(n, e)
     ref.order_apply(rank)
-    for alg in (tl.TL_APP, tl.TL_APM):
+    for alg in (tl.TL_APP, tl.TL_APM, tl.TL_AMM):
         nt, cnt, h, probes = g.list_count_hash(alg)
         _, rc, rh, rp = ref.list(alg, store=False)
         assert (nt, cnt, h, probes) == (rc, rc, rh, rp)
@@ -274,7 +275,7 @@ def test_every_tier_runs_and_matches():
                        ("random", synth.order_random(n, 4))]:
         g.order_apply(_dev(rank))
         ref.order_apply(rank)
-        for alg in (tl.TL_APP, tl.TL_APM):
+        for alg in (tl.TL_APP, tl.TL_APM, tl.TL_AMM):
             t, nt, probes, _ = g.list_collect(alg)
             st = tl.tl_last_list_stats(g.h)
             seen += np.array(st["tasks"]) > 0
@@ -307,7 +308,10 @@ def test_large_n_hash_probe_path():
     for name, rank in orders:
         g.order_apply(_dev(rank))
         ref.order_apply(rank)
-        for alg in (tl.TL_APP, tl.TL_APM):
+        # A-- only where the 150,000-neighbour hub is not last among its
+        # neighbours (else C-- >= 150,000^2 tests for the oracle)
+        algs = (tl.TL_APP, tl.TL_APM) + ((tl.TL_AMM,) if name == "identity" else ())
+        for alg in algs:
             nt, cnt, h, probes = g.list_count_hash(alg)
             _, rc, rh, rp = ref.list(alg, store=False)
             assert (nt, h, probes) == (rc, rh, rp), (name, alg)
@@ -364,7 +368,7 @@ def test_device_core_ordering_matches_oracle():
         g.order_apply(_dev(got))
         ref = oracle.Graph(n, e)
         ref.order_apply(want)
-        for alg in (tl.TL_APP, tl.TL_APM):
+        for alg in (tl.TL_APP, tl.TL_APM, tl.TL_AMM):
             assert g.cost(alg) == ref.cost(alg)
             nt, _, h, _ = g.list_count_hash(alg)
             _, rc, rh, _ = ref.list(alg, store=False)

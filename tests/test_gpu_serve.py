@@ -42,7 +42,7 @@ def pool():
         ref = oracle.Graph(n, e)
         for o, r in enumerate(orders):
             ref.order_apply(r)
-            for alg in (tl.TL_APP, tl.TL_APM):
+            for alg in (tl.TL_APP, tl.TL_APM, tl.TL_AMM):
                 _, c, h, _ = ref.list(alg, store=False)
                 want[(o, alg)] = (c, h)
         graphs.append((n, e, orders, want))
@@ -61,8 +61,9 @@ def _register(srv, pool):
 
 def _requests(pool, count, seed):
     rng = np.random.default_rng(seed)
-    return [(int(rng.integers(len(pool))), int(rng.integers(2)),
-             tl.TL_APP if rng.random() < 0.5 else tl.TL_APM) for _ in range(count)]
+    algs = (tl.TL_APP, tl.TL_APM, tl.TL_AMM)
+    return [(int(rng.integers(len(pool))), int(rng.integers(2)), algs[int(rng.integers(3))])
+            for _ in range(count)]
 
 
 def _run(srv, ids, reqs):

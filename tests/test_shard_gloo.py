@@ -39,7 +39,7 @@ def _rank_main(rank, world, port, q):
         out_off, out_adj = g.csr(0)
         in_off, in_adj = g.csr(1)
         res = {}
-        for alg in (oracle.APP, oracle.APM):
+        for alg in (oracle.APP, oracle.APM, oracle.AMM):
             work = shard.seed_work(out_off, out_adj, in_off, in_adj, alg)
             b, en = shard.balanced_ranges(work, world)[rank]
             _, c, h, p = g.list(alg, oracle.LITERAL, b, en, store=False)
@@ -59,7 +59,7 @@ def test_seed_work_sums_to_cost_and_ranges_partition():
     g.order_apply(r)
     out_off, out_adj = g.csr(0)
     in_off, in_adj = g.csr(1)
-    for alg in (oracle.APP, oracle.APM):
+    for alg in (oracle.APP, oracle.APM, oracle.AMM):
         w = shard.seed_work(out_off, out_adj, in_off, in_adj, alg)
         assert int(w.sum()) == g.cost(alg)  # Property 1, vertex by vertex summed
         for parts in (1, 2, 3, 7, 64):
@@ -88,7 +88,7 @@ def test_two_gloo_ranks_combine_to_the_full_listing():
     n, e, r = _graph()
     g = oracle.Graph(n, e)
     g.order_apply(r)
-    for alg in (oracle.APP, oracle.APM):
+    for alg in (oracle.APP, oracle.APM, oracle.AMM):
         _, c, h, p = g.list(alg, store=False)
         want = [c, int(np.uint64(h).astype(np.int64)), p, g.cost(alg)]
         assert out[0][alg] == want and out[1][alg] == want
