@@ -355,6 +355,9 @@ typedef struct {
   double kernel_ms[4];   /* summed device time of each kernel */
   uint64_t kernel_probes[4];     /* membership tests done by each kernel */
   uint64_t kernel_triangles[4];  /* triangles found by each kernel */
+  double bucketize_ms;           /* host wall time of the work split (a6) */
+  double consumer_ms;            /* host wall time inside the consumer */
+  double wall_ms;                /* host wall time of the whole call */
 } tl_list_stats;
 TL_EXPORT tl_status tl_last_list_stats(const tl_graph *g, tl_list_stats *out);
 

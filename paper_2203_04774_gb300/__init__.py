@@ -59,7 +59,9 @@ class RequestResult(ctypes.Structure):
 class ListStats(ctypes.Structure):
     _fields_ = [("launches", _U64), ("chunks", _U64), ("triangles", _U64), ("probes", _U64),
                 ("tasks", _U64 * 4), ("kernel_ms", ctypes.c_double * 4),
-                ("kernel_probes", _U64 * 4), ("kernel_triangles", _U64 * 4)]
+                ("kernel_probes", _U64 * 4), ("kernel_triangles", _U64 * 4),
+                ("bucketize_ms", ctypes.c_double), ("consumer_ms", ctypes.c_double),
+                ("wall_ms", ctypes.c_double)]
 
 
 SIGNATURES = {
@@ -284,7 +286,9 @@ def tl_last_list_stats(g) -> dict:
             "tasks": [int(v) for v in st.tasks],
             "kernel_ms": [float(v) for v in st.kernel_ms],
             "kernel_probes": [int(v) for v in st.kernel_probes],
-            "kernel_triangles": [int(v) for v in st.kernel_triangles]}
+            "kernel_triangles": [int(v) for v in st.kernel_triangles],
+            "bucketize_ms": float(st.bucketize_ms), "consumer_ms": float(st.consumer_ms),
+            "wall_ms": float(st.wall_ms)}
 
 
 def tl_kernel_launches() -> int:

@@ -1,6 +1,7 @@
 // C ABI of libtl (declared in include/tl.h).
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -230,7 +231,13 @@ tl_status list_impl(tl_graph *G, int alg, uint32_t xb, uint32_t xe, size_t chunk
   const uint64_t cap = chunk_bytes / 12;
   if (cap < tl::kSlabCap) tl::fail(TL_EINVAL, "chunk too small for one task");
   cudaStream_t s = g.stream;
+  const auto t_call = std::chrono::steady_clock::now();
+  auto ms_since = [](std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+        .count();
+  };
   bucketize(G, alg, xb, xe);
+  const double bucketize_ms = ms_since(t_call);
 
   uint64_t slab_words = 0, max_tasks = 1;
   for (int t = 0; t < 2; ++t) {  // warp tiers: one global slab per warp
@@ -302,9 +309,12 @@ tl_status list_impl(tl_graph *G, int alg, uint32_t xb, uint32_t xe, size_t chunk
   uint64_t pending_n = 0;
   bool stopped = false;
   int ph = 0;
+  double consumer_ms = 0;
   auto deliver = [&](int which, uint64_t cnt) {
     if (cb && cnt > 0 && !stopped) {
+      const auto t0 = std::chrono::steady_clock::now();
       if (cb(chunk[which], cnt, chunk_idx, user) != 0) stopped = true;
+      consumer_ms += ms_since(t0);
     }
     if (cnt > 0) ++chunk_idx;
     st.chunks = chunk_idx;
@@ -403,6 +413,9 @@ tl_status list_impl(tl_graph *G, int alg, uint32_t xb, uint32_t xe, size_t chunk
   if (n_probes) *n_probes = total_probes;
   st.triangles = total_tri;
   st.probes = total_probes;
+  st.bucketize_ms = bucketize_ms;
+  st.consumer_ms = consumer_ms;
+  st.wall_ms = ms_since(t_call);
   G->stats = st;
   if (stopped) tl::fail(TL_ECALLBACK, "the consumer asked to stop");
   TL_API_END
