@@ -99,6 +99,36 @@ __global__ void k_union_ranks(const uint32_t *const *__restrict__ src, uint64_t 
   }
 }
 
+// CSR offsets of the union: out[j] = ebase[p] + src[p][j - vbase[p]] for the
+// part p holding vertex j (the entry off[n] is written by the host).
+__global__ void k_union_offsets(const uint64_t *const *__restrict__ src, uint64_t total,
+                                uint32_t k, const uint64_t *__restrict__ vbase,
+                                const uint64_t *__restrict__ ebase, uint64_t *__restrict__ out) {
+  __shared__ uint32_t s_lo, s_hi;
+  const uint64_t t0 = (uint64_t)blockIdx.x * kTile;
+  const uint64_t t1 = min(total, t0 + kTile);
+  tile_parts(vbase, k, t0, t1, &s_lo, &s_hi);
+  for (uint64_t j = t0 + threadIdx.x; j < t1; j += kThreads) {
+    const uint32_t p = part_of(vbase, s_lo, s_hi, j);
+    out[j] = __ldg(ebase + p) + src[p][j - __ldg(vbase + p)];
+  }
+}
+
+// CSR lists of the union: out[j] = vbase[p] + src[p][j - ebase[p]] (ranks
+// shifted into the part's range) for the part p holding entry j.
+__global__ void k_union_adj(const uint32_t *const *__restrict__ src, uint64_t total, uint32_t k,
+                            const uint64_t *__restrict__ ebase, const uint64_t *__restrict__ vbase,
+                            uint32_t *__restrict__ out) {
+  __shared__ uint32_t s_lo, s_hi;
+  const uint64_t t0 = (uint64_t)blockIdx.x * kTile;
+  const uint64_t t1 = min(total, t0 + kTile);
+  tile_parts(ebase, k, t0, t1, &s_lo, &s_hi);
+  for (uint64_t j = t0 + threadIdx.x; j < t1; j += kThreads) {
+    const uint32_t p = part_of(ebase, s_lo, s_hi, j);
+    out[j] = (uint32_t)__ldg(vbase + p) + src[p][j - __ldg(ebase + p)];
+  }
+}
+
 template <class T>
 T read_back(const T *dev, cudaStream_t s) {
   T v;
@@ -162,6 +192,83 @@ void build_edge_set_parts(DeviceGraph &g, uint32_t k, const uint32_t *n, const u
   finish_edge_set(g, total);
 }
 
+namespace {
+
+// The union of parts that all hold their DAG under the ordering to use:
+// every array of the union is the parts' arrays concatenated, vertex ids and
+// ranks shifted by vbase and list offsets by ebase; the costs add up.  Moves
+// about 32 bytes per edge, against a full relabel-and-sort for build_dag.
+void union_of_dags(DeviceGraph &u, uint32_t k, const DeviceGraph *const *parts,
+                   const std::vector<uint64_t> &vb, const std::vector<uint64_t> &eb) {
+  cudaStream_t s = u.stream;
+  const uint32_t n = u.n;
+  const uint64_t m = u.m;
+  // table: vbase | ebase | pointers: E, rank, inv, out_off, in_off, out_adj, in_adj
+  constexpr int kPtr = 7;
+  std::vector<const void *> ptr((size_t)kPtr * k);
+  uint64_t cpp = 0, cpm = 0, cmm = 0;
+  uint32_t mxo = 0, mxi = 0;
+  for (uint32_t i = 0; i < k; ++i) {
+    const DeviceGraph &g = *parts[i];
+    const void *p[kPtr] = {g.E.p, g.rank.p, g.inv.p, g.out_off.p, g.in_off.p, g.out_adj.p,
+                           g.in_adj.p};
+    for (int j = 0; j < kPtr; ++j) ptr[(size_t)j * k + i] = p[j];
+    cpp += g.cost_app;
+    cpm += g.cost_apm;
+    cmm += g.cost_amm;
+    mxo = g.max_out_deg > mxo ? g.max_out_deg : mxo;
+    mxi = g.max_in_deg > mxi ? g.max_in_deg : mxi;
+  }
+  DevBuf table(s);
+  table.reserve((2 * (uint64_t)k + 2 + (uint64_t)kPtr * k) * 8);
+  uint64_t *d_vb = table.as<uint64_t>(), *d_eb = d_vb + (k + 1);
+  const void **d_ptr = reinterpret_cast<const void **>(d_eb + (k + 1));
+  TL_CUDA(cudaMemcpyAsync(d_vb, vb.data(), (k + 1) * 8, cudaMemcpyHostToDevice, s));
+  TL_CUDA(cudaMemcpyAsync(d_eb, eb.data(), (k + 1) * 8, cudaMemcpyHostToDevice, s));
+  TL_CUDA(cudaMemcpyAsync(d_ptr, ptr.data(), ptr.size() * 8, cudaMemcpyHostToDevice, s));
+  auto col = [&](int j) { return d_ptr + (size_t)j * k; };
+  u.E.reserve((m ? m : 1) * 8);
+  u.rank.reserve((uint64_t)n * 4);
+  u.inv.reserve((uint64_t)n * 4);
+  u.out_off.reserve(((uint64_t)n + 1) * 8);
+  u.in_off.reserve(((uint64_t)n + 1) * 8);
+  u.out_adj.reserve((m + 4) * 4);
+  u.in_adj.reserve((m + 4) * 4);
+  if (m) {
+    k_union_keys<<<tiles(m), kThreads, 0, s>>>(
+        reinterpret_cast<const uint64_t *const *>(col(0)), m, k, d_eb, d_vb, u.E.as<uint64_t>());
+    TL_CHECK_LAUNCH();
+    for (int j = 5; j <= 6; ++j) {
+      k_union_adj<<<tiles(m), kThreads, 0, s>>>(
+          reinterpret_cast<const uint32_t *const *>(col(j)), m, k, d_eb, d_vb,
+          (j == 5 ? u.out_adj : u.in_adj).as<uint32_t>());
+      TL_CHECK_LAUNCH();
+    }
+  }
+  for (int j = 1; j <= 2; ++j) {
+    k_union_ranks<<<tiles(n), kThreads, 0, s>>>(reinterpret_cast<const uint32_t *const *>(col(j)),
+                                                n, k, d_vb,
+                                                (j == 1 ? u.rank : u.inv).as<uint32_t>());
+    TL_CHECK_LAUNCH();
+  }
+  for (int j = 3; j <= 4; ++j) {
+    uint64_t *off = (j == 3 ? u.out_off : u.in_off).as<uint64_t>();
+    k_union_offsets<<<tiles(n), kThreads, 0, s>>>(
+        reinterpret_cast<const uint64_t *const *>(col(j)), n, k, d_vb, d_eb, off);
+    TL_CHECK_LAUNCH();
+    TL_CUDA(cudaMemcpyAsync(off + n, &eb[k], 8, cudaMemcpyHostToDevice, s));
+  }
+  TL_CUDA(cudaStreamSynchronize(s));  // the host tables outlive their copies
+  u.cost_app = cpp;
+  u.cost_apm = cpm;
+  u.cost_amm = cmm;
+  u.max_out_deg = mxo;
+  u.max_in_deg = mxi;
+  u.ordered = true;
+}
+
+}  // namespace
+
 void build_union(DeviceGraph &u, uint32_t k, const DeviceGraph *const *parts,
                  const uint32_t *const *rank) {
   cudaStream_t s = u.stream;
@@ -178,6 +285,14 @@ void build_union(DeviceGraph &u, uint32_t k, const DeviceGraph *const *parts,
   const std::vector<uint64_t> eb = prefix(k, mv.data(), ~0ull >> 4, "too many edges");
   u.n = (uint32_t)vb[k];
   u.m = eb[k];
+  bool dags = true;  // every part holds its DAG and keeps its ordering
+  for (uint32_t i = 0; i < k && dags; ++i)
+    dags = parts[i]->ordered && !(rank && rank[i]);
+  if (dags) {
+    union_of_dags(u, k, parts, vb, eb);
+    u.part_vbase = vb;
+    return;
+  }
   // table: vbase[k+1] | ebase[k+1] | E pointers[k] | rank pointers[k]
   DevBuf table(s), rank_u(s);
   table.reserve((4 * (uint64_t)k + 2) * 8);

@@ -30,9 +30,8 @@ uint64_t now_ns() {
 
 struct Request {
   uint64_t id = 0;
-  const tl_graph *g = nullptr;   // copied from the registry at submit, so that
-  const uint32_t *rank = nullptr;  // workers never read the registry
-  uint32_t n = 0;
+  const tl_graph *g = nullptr;  // the prepared handle, copied from the registry at
+  uint32_t n = 0;               // submit so that workers never read the registry
   tl_alg alg = TL_APP;
   uint64_t footprint = 0;
   bool done = false;
@@ -43,7 +42,10 @@ struct GraphEntry {
   const tl_graph *g = nullptr;
   uint32_t n = 0;
   uint64_t m = 0;
-  std::vector<uint32_t *> ranks;  // device, n each, owned by the server
+  // one handle per registered ordering, owned by the server: a copy of the
+  // graph with its DAG built under that ordering, so that a batch's union
+  // only concatenates the parts' arrays
+  std::vector<tl_graph *> prepared;
 };
 
 struct Worker {
@@ -63,6 +65,7 @@ struct tl_server {
   std::deque<Request *> pending;
   std::unordered_map<uint64_t, Request *> requests;
   std::vector<GraphEntry> graphs;
+  std::vector<cudaStream_t> streams;  // the streams the prepared handles were built on
   uint64_t in_use = 0, next_id = 1;
   bool stop = false;
   std::vector<Worker> workers;
@@ -78,18 +81,17 @@ void run_batch(tl_server *S, Worker &W, std::vector<Request *> &batch) {
                    [](const Request *a, const Request *b) { return a->alg < b->alg; });
   const uint32_t k = (uint32_t)batch.size();
   std::vector<const tl_graph *> parts(k);
-  std::vector<const uint32_t *> ranks(k);
   std::vector<uint64_t> vb(k + 1, 0);
   for (uint32_t i = 0; i < k; ++i) {
     parts[i] = batch[i]->g;
-    ranks[i] = batch[i]->rank;
     vb[i + 1] = vb[i] + batch[i]->n;
   }
   tl_status st = TL_OK;
   std::vector<uint64_t> counts(k, 0), hashes(k, 0);
   tl_graph *u = nullptr;
   if (cudaSetDevice(S->device) != cudaSuccess) st = TL_ECUDA;
-  if (st == TL_OK) st = tl_graph_union(&u, parts.data(), ranks.data(), k, W.stream);
+  // the parts keep their own orderings: the union concatenates their DAGs
+  if (st == TL_OK) st = tl_graph_union(&u, parts.data(), nullptr, k, W.stream);
   if (st == TL_OK) {
     tl_count_hash_parts_state cs{W.d_vbase, k, W.d_counts, W.d_hashes, W.cstream};
     bool ok = cudaMemcpyAsync(W.d_vbase, vb.data(), (k + 1) * 8, cudaMemcpyHostToDevice,
@@ -198,7 +200,11 @@ void destroy(tl_server *S) {
     if (W.cstream) cudaStreamDestroy(W.cstream);
   }
   for (GraphEntry &ge : S->graphs)
-    for (uint32_t *r : ge.ranks) cudaFree(r);
+    for (tl_graph *h : ge.prepared) tl_graph_free(h);
+  for (cudaStream_t st : S->streams) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
   for (auto &kv : S->requests) delete kv.second;
   delete S;
 }
@@ -275,36 +281,48 @@ tl_status tl_server_add_ordering(tl_server *S, uint32_t graph_id, const uint32_t
                                  int rank_on_device, uint32_t *ordering_id) {
   TL_SERVE_BEGIN
   if (!S || !rank || !ordering_id) tl::fail(TL_EINVAL, "NULL argument");
+  const tl_graph *g = nullptr;
   uint32_t n = 0;
   {
     std::lock_guard<std::mutex> lk(S->mu);
     if (graph_id >= S->graphs.size()) tl::fail(TL_EINVAL, "unknown graph_id");
+    g = S->graphs[graph_id].g;
     n = S->graphs[graph_id].n;
   }
   TL_CUDA(cudaSetDevice(S->device));
-  uint32_t *d = nullptr;
   cudaStream_t s = nullptr;
-  TL_CUDA(cudaMalloc(&d, (uint64_t)n * 4 + 4));  // + 4: the check's flag
+  uint32_t *d = nullptr;
+  tl_graph *h = nullptr;
+  tl_status st = TL_OK;
   try {
     TL_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-    TL_CUDA(cudaMemcpyAsync(d, rank, (uint64_t)n * 4,
-                            rank_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                            s));
-    if (!tl::is_permutation(d, n, d + n, s))
-      tl::fail(TL_EINVAL, "tl_server_add_ordering: rank is not a permutation of [0, n)");
-    cudaStreamDestroy(s);
-  } catch (...) {
-    if (s) {
-      cudaStreamSynchronize(s);
-      cudaStreamDestroy(s);
+    const uint32_t *dev_rank = rank;
+    if (!rank_on_device) {
+      TL_CUDA(cudaMalloc(&d, (uint64_t)n * 4 + 4));
+      TL_CUDA(cudaMemcpyAsync(d, rank, (uint64_t)n * 4, cudaMemcpyHostToDevice, s));
+      dev_rank = d;
     }
-    cudaFree(d);
+    // a one-part union: a copy of the graph with its DAG under this ordering
+    // (not a permutation -> TL_EINVAL)
+    st = tl_graph_union(&h, &g, &dev_rank, 1, s);
+  } catch (...) {
+    if (s) cudaStreamSynchronize(s);
+    if (d) cudaFree(d);
+    if (s) cudaStreamDestroy(s);
     throw;
   }
+  cudaStreamSynchronize(s);
+  if (d) cudaFree(d);
+  if (st != TL_OK) {
+    cudaStreamDestroy(s);
+    return st;
+  }
+  // the handle's buffers are released on s: s lives until the server is freed
   std::lock_guard<std::mutex> lk(S->mu);
   GraphEntry &ge = S->graphs[graph_id];
-  ge.ranks.push_back(d);
-  *ordering_id = (uint32_t)(ge.ranks.size() - 1);
+  ge.prepared.push_back(h);
+  S->streams.push_back(s);
+  *ordering_id = (uint32_t)(ge.prepared.size() - 1);
   TL_SERVE_END
 }
 
@@ -318,14 +336,13 @@ tl_status tl_server_submit(tl_server *S, uint32_t graph_id, uint32_t ordering_id
   r->res.t_submit_ns = now_ns();
   {
     std::lock_guard<std::mutex> lk(S->mu);
-    if (graph_id >= S->graphs.size() || ordering_id >= S->graphs[graph_id].ranks.size()) {
+    if (graph_id >= S->graphs.size() || ordering_id >= S->graphs[graph_id].prepared.size()) {
       delete r;
       tl::fail(TL_EINVAL, "unknown graph_id or ordering_id");
     }
     const GraphEntry &ge = S->graphs[graph_id];
     r->id = S->next_id++;
-    r->g = ge.g;
-    r->rank = ge.ranks[ordering_id];
+    r->g = ge.prepared[ordering_id];
     r->n = ge.n;
     r->alg = alg;
     r->footprint = footprint(ge.n, ge.m);

@@ -279,3 +279,34 @@ def test_union_invalid_inputs():
     u.free()
     a.free()
     b.free()
+
+
+def test_union_of_ordered_graphs_concatenates_their_dags():
+    """When every part holds its DAG and no rank is given, the union's DAG is
+    assembled by concatenation; it must equal byte for byte the DAG built by
+    relabel-and-sort from the same per-part orderings."""
+    parts = _parts_small()
+    graphs = [tl.Graph(n, _dev(e)) for n, e in parts]
+    ranks = []
+    for (n, e), g in zip(parts, graphs):
+        off, _ = synth.simple_csr(n, e)
+        r = synth.order_degree(off) if n % 2 else synth.order_random(n, n)
+        g.order_apply(_dev(r))
+        ranks.append(r)
+    fast = tl.Graph.union(graphs)                         # concatenated DAGs
+    slow = tl.Graph.union(graphs, [_dev(r) for r in ranks])  # relabel + sort
+    for d in (0, 1):
+        fo, fa = fast.csr(d)
+        so, sa = slow.csr(d)
+        assert np.array_equal(fo, so) and np.array_equal(fa, sa), d
+    for alg in (tl.TL_APP, tl.TL_APM, tl.TL_AMM):
+        assert fast.cost(alg) == slow.cost(alg)
+    _check_union(fast, parts, ranks, [tl.TL_APP, tl.TL_APM, tl.TL_AMM] * 3 + [tl.TL_APP])
+    # the union's own orderings still work (its edge set is concatenated too)
+    r = fast.order_compute(tl.TL_ORDER_DEGREE)
+    fast.order_apply(r)
+    assert fast.list_count_hash(tl.TL_APM)[0] == slow.list_count_hash(tl.TL_APM)[0]
+    fast.free()
+    slow.free()
+    for g in graphs:
+        g.free()
