@@ -27,15 +27,21 @@ cudaMemPool_t device_pool() {
   int dev = 0;
   TL_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) fail(TL_EINVAL, "device index out of range");
-  std::lock_guard<std::mutex> lock(mu);
-  if (!pools[dev]) {
-    cudaMemPool_t p;
-    TL_CUDA(cudaDeviceGetDefaultMemPool(&p, dev));
-    uint64_t keep = 8ull << 30;  // cached for reuse; the rest goes back at sync points
-    TL_CUDA(cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep));
-    pools[dev] = p;
+  cudaMemPool_t p;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) TL_CUDA(cudaDeviceGetDefaultMemPool(&pools[dev], dev));
+    p = pools[dev];
   }
-  return pools[dev];
+  // The threshold counts every reserved byte, in use or not: keep it 32 GiB
+  // above what is in use, so that up to 32 GiB of freed buffers stay cached
+  // for the next call however much long-lived memory (resident graphs) the
+  // pool holds, and the rest goes back to the driver at sync points.
+  uint64_t used = 0;
+  TL_CUDA(cudaMemPoolGetAttribute(p, cudaMemPoolAttrUsedMemCurrent, &used));
+  uint64_t keep = used + (32ull << 30);
+  TL_CUDA(cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep));
+  return p;
 }
 
 namespace {

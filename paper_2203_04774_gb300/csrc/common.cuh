@@ -44,9 +44,10 @@ inline void fail(tl_status s, const std::string &msg) { throw Error{s, msg}; }
 
 // ---- device buffer (RAII, stream-ordered) ------------------------------------
 
-// The current device's default memory pool, set once per device to keep up
-// to 8 GiB of freed memory cached (release threshold) so that buffers of
-// repeated calls are recycled without driver round trips.
+// The current device's default memory pool; each call sets its release
+// threshold to the bytes in use + 8 GiB, so that up to 8 GiB of freed memory
+// stays cached and buffers of repeated calls are recycled without driver
+// round trips.
 cudaMemPool_t device_pool();
 
 // Allocations come from the device pool in stream order on `stream` (the

@@ -817,21 +817,40 @@ __global__ void k_count_hash(const uint32_t *__restrict__ t, uint64_t n,
 // Per-part count and set hash of a disjoint union's triples: a triple's part
 // is the one whose vertex range [vbase[p], vbase[p+1]) holds its ids, and it is
 // hashed with part-local ids, so a part's (count, H) is the one it has alone.
-// A warp whose 32 triples share one part adds them with one atomic pair.
+// Each warp walks a contiguous range of the chunk (triples of one task, hence
+// of one part, are contiguous) and keeps running sums while the part stays
+// the same, adding them to the part's counters only when the part changes
+// and at the end of its range.
 __global__ void k_count_hash_parts(const uint32_t *__restrict__ t, uint64_t n,
                                    const uint64_t *__restrict__ vbase, uint32_t k,
                                    unsigned long long *__restrict__ counts,
                                    unsigned long long *__restrict__ hashes) {
   const int lane = threadIdx.x & 31;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t w0 = blockIdx.x * (uint64_t)blockDim.x + (threadIdx.x & ~31u); w0 < n;
-       w0 += stride) {
-    const uint64_t i = w0 + lane;
-    const bool valid = i < n;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  const uint64_t w = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  const uint64_t per = ((n + warps - 1) / warps + 31) & ~31ull;
+  const uint64_t r0 = w * per, r1 = r0 + per < n ? r0 + per : n;
+  uint32_t cur = 0xffffffffu;  // the part of the running sums (the same in every lane)
+  unsigned long long acc_c = 0, acc_h = 0;
+  auto flush = [&]() {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      acc_c += __shfl_down_sync(0xffffffffu, acc_c, d);
+      acc_h += __shfl_down_sync(0xffffffffu, acc_h, d);
+    }
+    if (lane == 0 && cur != 0xffffffffu && acc_c) {
+      atomicAdd(counts + cur, acc_c);
+      atomicAdd(hashes + cur, acc_h);
+    }
+    acc_c = acc_h = 0;
+  };
+  for (uint64_t b = r0; b < r1; b += 32) {
+    const uint64_t i = b + lane;
+    const bool valid = i < r1;
     uint32_t p = 0xffffffffu;
     unsigned long long h = 0;
     if (valid) {
-      const uint32_t a = __ldcs(t + 3 * i), b = __ldcs(t + 3 * i + 1), c = __ldcs(t + 3 * i + 2);
+      const uint32_t a = __ldcs(t + 3 * i), bb = __ldcs(t + 3 * i + 1), c = __ldcs(t + 3 * i + 2);
       uint32_t lo = 0, hi = k - 1;
       while (lo < hi) {
         const uint32_t mid = (lo + hi + 1) >> 1;
@@ -839,22 +858,26 @@ __global__ void k_count_hash_parts(const uint32_t *__restrict__ t, uint64_t n,
       }
       p = lo;
       const uint32_t o = (uint32_t)__ldg(vbase + p);
-      h = triple_hash(a - o, b - o, c - o);
+      h = triple_hash(a - o, bb - o, c - o);
     }
     const uint32_t p0 = __shfl_sync(0xffffffffu, p, 0);
     if (__all_sync(0xffffffffu, !valid || p == p0)) {
-      const unsigned cnt = __popc(__ballot_sync(0xffffffffu, valid));
-#pragma unroll
-      for (int d = 16; d > 0; d >>= 1) h += __shfl_down_sync(0xffffffffu, h, d);
-      if (lane == 0) {
-        atomicAdd(counts + p0, (unsigned long long)cnt);
-        atomicAdd(hashes + p0, h);
+      if (p0 != cur) {
+        flush();
+        cur = p0;
       }
-    } else if (valid) {
-      atomicAdd(counts + p, 1ull);
-      atomicAdd(hashes + p, h);
+      acc_c += valid ? 1 : 0;
+      acc_h += h;
+    } else {  // a part boundary inside these 32 triples
+      flush();
+      cur = 0xffffffffu;
+      if (valid) {
+        atomicAdd(counts + p, 1ull);
+        atomicAdd(hashes + p, h);
+      }
     }
   }
+  flush();
 }
 
 template <class K>

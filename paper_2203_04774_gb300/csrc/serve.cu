@@ -65,7 +65,8 @@ struct tl_server {
   std::deque<Request *> pending;
   std::unordered_map<uint64_t, Request *> requests;
   std::vector<GraphEntry> graphs;
-  std::vector<cudaStream_t> streams;  // the streams the prepared handles were built on
+  cudaStream_t reg_stream = nullptr;  // prepared handles are built (and freed) on it
+  std::mutex reg_mu;                  // one registration at a time on reg_stream
   uint64_t in_use = 0, next_id = 1;
   bool stop = false;
   std::vector<Worker> workers;
@@ -201,9 +202,9 @@ void destroy(tl_server *S) {
   }
   for (GraphEntry &ge : S->graphs)
     for (tl_graph *h : ge.prepared) tl_graph_free(h);
-  for (cudaStream_t st : S->streams) {
-    cudaStreamSynchronize(st);
-    cudaStreamDestroy(st);
+  if (S->reg_stream) {
+    cudaStreamSynchronize(S->reg_stream);
+    cudaStreamDestroy(S->reg_stream);
   }
   for (auto &kv : S->requests) delete kv.second;
   delete S;
@@ -246,6 +247,7 @@ tl_status tl_server_create(tl_server **out, const tl_server_config *cfg) {
   S->cfg = *cfg;
   try {
     TL_CUDA(cudaGetDevice(&S->device));
+    TL_CUDA(cudaStreamCreateWithFlags(&S->reg_stream, cudaStreamNonBlocking));
     S->batch_fixed = tl::list_fixed_bytes(cfg->chunk_bytes);
     S->workers.resize(cfg->workers);
     for (Worker &W : S->workers) {
@@ -290,38 +292,23 @@ tl_status tl_server_add_ordering(tl_server *S, uint32_t graph_id, const uint32_t
     n = S->graphs[graph_id].n;
   }
   TL_CUDA(cudaSetDevice(S->device));
-  cudaStream_t s = nullptr;
-  uint32_t *d = nullptr;
+  std::lock_guard<std::mutex> reg(S->reg_mu);
+  cudaStream_t s = S->reg_stream;
+  tl::DevBuf d(s);  // host ranks are staged on the device
+  const uint32_t *dev_rank = rank;
+  if (!rank_on_device) {
+    d.reserve((uint64_t)n * 4);
+    TL_CUDA(cudaMemcpyAsync(d.p, rank, (uint64_t)n * 4, cudaMemcpyHostToDevice, s));
+    dev_rank = d.as<uint32_t>();
+  }
+  // a one-part union: a copy of the graph with its DAG under this ordering
+  // (not a permutation -> TL_EINVAL)
   tl_graph *h = nullptr;
-  tl_status st = TL_OK;
-  try {
-    TL_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-    const uint32_t *dev_rank = rank;
-    if (!rank_on_device) {
-      TL_CUDA(cudaMalloc(&d, (uint64_t)n * 4 + 4));
-      TL_CUDA(cudaMemcpyAsync(d, rank, (uint64_t)n * 4, cudaMemcpyHostToDevice, s));
-      dev_rank = d;
-    }
-    // a one-part union: a copy of the graph with its DAG under this ordering
-    // (not a permutation -> TL_EINVAL)
-    st = tl_graph_union(&h, &g, &dev_rank, 1, s);
-  } catch (...) {
-    if (s) cudaStreamSynchronize(s);
-    if (d) cudaFree(d);
-    if (s) cudaStreamDestroy(s);
-    throw;
-  }
-  cudaStreamSynchronize(s);
-  if (d) cudaFree(d);
-  if (st != TL_OK) {
-    cudaStreamDestroy(s);
-    return st;
-  }
-  // the handle's buffers are released on s: s lives until the server is freed
+  const tl_status st = tl_graph_union(&h, &g, &dev_rank, 1, s);
+  if (st != TL_OK) return st;
   std::lock_guard<std::mutex> lk(S->mu);
   GraphEntry &ge = S->graphs[graph_id];
   ge.prepared.push_back(h);
-  S->streams.push_back(s);
   *ordering_id = (uint32_t)(ge.prepared.size() - 1);
   TL_SERVE_END
 }
