@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtl.so")
-SOURCES = ["api.cu", "batch.cu", "build.cu", "core.cu", "list.cu", "noalloc.cu", "scan.cu", "serve.cu",
+SOURCES = ["api.cu", "batch.cu", "build.cu", "consumer.cu", "core.cu", "list.cu", "noalloc.cu", "scan.cu", "serve.cu",
            "sort.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden",
