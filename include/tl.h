@@ -323,7 +323,9 @@ TL_EXPORT tl_status tl_server_create(tl_server **out, const tl_server_config *cf
 /* Register g (caller-owned, loaded on the current device) -> *graph_id. */
 TL_EXPORT tl_status tl_server_add_graph(tl_server *s, const tl_graph *g, uint32_t *graph_id);
 /* Register an ordering of a registered graph: rank[v] = pi_v - 1, n uint32,
- * host or device pointer (copied).  Not a permutation -> TL_EINVAL. */
+ * host or device pointer (read during the call).  The server builds and keeps
+ * a copy of the graph with its DAG under this ordering (16 m + 24 n bytes of
+ * device memory until tl_server_free).  Not a permutation -> TL_EINVAL. */
 TL_EXPORT tl_status tl_server_add_ordering(tl_server *s, uint32_t graph_id, const uint32_t *rank,
                                            int rank_on_device, uint32_t *ordering_id);
 /* Queue a request; returns at once with its id. */
