@@ -24,6 +24,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -361,11 +362,20 @@ def read_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def code_only(src: str) -> str:
+    """C++ source without comments, blank lines and trailing spaces."""
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    return "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
+
+
 def list_source_hash():
+    """Hash of the listing kernels' code (list.cu + list.cuh, comments ignored):
+    recorded DRAM counters are used only while it matches."""
     h = hashlib.sha256()
     for f in ("list.cu", "list.cuh"):
-        with open(os.path.join(ROOT, "paper_2203_04774_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2203_04774_gb300", "csrc", f)) as fh:
+            h.update(code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

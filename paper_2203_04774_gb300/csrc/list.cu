@@ -1,33 +1,40 @@
-// Triangle listing: Algorithm 1 (A++) and Algorithm 2 (A+-) of Sec. 2.1.
+// Triangle listing: Algorithm 1 (A++), Algorithm 2 (A+-) and the third
+// variant A-- of Sec. 2.1.
 //
-// Both algorithms have the same shape once the "B vertex" x is fixed:
-//   A++: x = w, probe set P_x = N-_w, scanned lists N+_y for y in P_x.
-//   A+-: x = u, probe set P_x = N+_u, scanned lists N+_y for y in P_x.
-// For every y in P_x and every z in N+_y, z in P_x reports triangle {x, y, z}
-// (A++: u=y, v=z, w=x; A+-: u=x, v=y, w=z).  The number of membership tests
-// is sum_{y in P_x} d+_y per x; summed over x it is C++ resp. C+- (Property 1).
+// The three algorithms have the same shape once the "B vertex" x is fixed:
+//   A++: x = w, probe set P_x = N-_w, seeds y in N-_w, scanned lists N+_y;
+//   A+-: x = u, probe set P_x = N+_u, seeds y in N+_u, scanned lists N+_y;
+//   A--: x = v, probe set P_x = N-_v, seeds y in N+_v, scanned lists N-_y.
+// For every seed y and every z in its scanned list, z in P_x reports a
+// triangle {x, y, z} (A++: u=y, v=z, w=x; A+-: u=x, v=y, w=z; A--: u=z, v=x,
+// w=y).  The membership tests of x number the sum of its seeds' list
+// lengths; summed over x they are C++, C+- resp. C-- (Property 1).
 //
-// Work space (a6).  Seed edge k = (x, y_k) is the k-th entry of the
-// probe-side CSR; it owns the d+(y_k) tests [WP[k], WP[k+1]) of a global
-// exclusive prefix WP.  Every kernel walks the tests of a range with the same
-// warp-level mapping (scan_items): a window of 32 consecutive seed edges is
-// held one per lane, each 32-test step finds every lane's seed edge by a
-// shuffle binary search over the window, so all lanes work whatever the list
-// lengths are.
+// Work space (a6).  Seed edge k = (x, y_k) is the k-th entry of the seed-side
+// CSR; it owns the tests [WP[k], WP[k+1]) of a global exclusive prefix WP.
+// Every kernel walks the tests of a range with the same warp-level mapping
+// (scan_items): a window of 32 consecutive seed edges is held one per lane;
+// a list of at least 32 tests is streamed with 16-byte loads, shorter ones
+// share 32-test steps in which each lane finds its seed edge by a shuffle
+// binary search over the window, so all lanes work whatever the lengths.
 //
-// B (the boolean array of Algorithms 1 and 2) per tier:
-//   small/medium x: a per-warp open-addressing hash table in shared memory
-//   (load <= 1/2), one warp per x, vertices grouped into tasks of ~2^14 tests;
-//   large x: one table per CTA -- a bitmap over all ranks when n is small
-//   enough (literally B, bit-packed), else a hash table, else binary search
-//   in the sorted row -- and the work cut into pieces shared by the CTA's warps.
+// B (the boolean array of the algorithms) per tier:
+//   small/medium x: a per-warp hash table in shared memory (load <= 1/2), one
+//   warp per x, vertices grouped into tasks of about kWarpWork tests;
+//   mid/large x: one structure per CTA -- a bucketed hash, a bitmap over all
+//   ranks when n is small enough (literally B, bit-packed), a shared filter in
+//   front of a global hash for hubs of large graphs, or binary search in the
+//   sorted row -- and the work cut into pieces shared by the CTA's warps.
 //
-// Output (a9).  Hits are compacted per warp (ballot) into the CTA's private
-// slab as sorted original-id triples.  At the end of a task one atomic
-// reserves room in the current output chunk and the CTA copies the slab.
-// If the chunk is full the task is queued for the next launch (after the
-// consumer has drained the chunk) and nothing of it is written, so every
-// chunk holds whole tasks and the listing resumes exactly where it stopped.
+// Output (a9).  Warp tiers: a task's hits go to the warp's global slab; at its
+// end one atomic reserves room in the current chunk and the warp copies them,
+// or the whole task is queued for the next launch.  CTA tiers: each warp
+// stages hits in shared memory and copies them to the chunk itself (one
+// atomic per flush); a warp whose reservation fails stops, and the exact test
+// ranges whose hits were not written go to the next launch, one record per
+// piece.  Either way every chunk holds complete output for the tests it
+// covers, and the listing resumes exactly where it stopped.
+
 #include "list.cuh"
 
 namespace tl {

@@ -8,7 +8,7 @@ namespace tl {
 // Tiers of B vertices x (by probe-set size p = |P_x| and work W_x):
 //   0 small:  p <= 32,   W <= kWarpWork  -- one warp per x, 64-slot hash per warp
 //   1 medium: p <= 1024, W <= kWarpWork  -- one warp per x, 2048-slot hash per warp
-//   2 mid:    p <= 2048, W >  kWarpWork  -- 256-thread CTA per piece, 8192-slot hash
+//   2 mid:    p <= 2048, W >  kWarpWork  -- 256-thread CTA per piece, 8192-slot bucketed hash
 //   3 large:  p >  2048                  -- 1024-thread CTA per piece, bitmap / hash
 constexpr int kTiers = 4;
 constexpr int kWarpThreads = 256;
@@ -112,7 +112,7 @@ struct ListArgs {
   ListCtl *ctl;
   uint32_t *chunk;               // output chunk, 3 uint32 per triangle
   uint64_t chunk_cap;            // triangles
-  uint32_t *slabs;               // per-CTA staging, slab_cap triangles each
+  uint32_t *slabs;               // warp tiers: per-warp staging, slab_cap triangles each
   uint64_t slab_cap;
   const uint32_t *retry_in;      // warp tiers: tasks left over by the previous launch
   uint32_t n_retry;              // entries in retry_in / rr_in
