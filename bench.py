@@ -609,9 +609,18 @@ def ordering_sweep(tl, n, e, e_dev, stream):
     """GPU listing time vs the paper's cost for several orderings (Fig. 2 analogue)."""
     from paper_2203_04774_gb300 import synth
     off, adj = synth.simple_csr(n, e)
-    orders = {"random": synth.order_random(n, 2), "degree": synth.order_degree(off),
-              "core": synth.order_core(off, adj), "split": synth.order_split(off),
-              "check": synth.order_check(off, adj)}
+    makers = {"random": lambda: synth.order_random(n, 2),
+              "degree": lambda: synth.order_degree(off),
+              "core": lambda: synth.order_core(off, adj),
+              "split": lambda: synth.order_split(off),
+              "check": lambda: synth.order_check(off, adj),
+              "neigh": lambda: synth.order_neigh(off, adj)[0],
+              "neigh_c++": lambda: synth.order_neigh(off, adj, objective="C++")[0]}
+    orders, host_s = {}, {}
+    for name, make in makers.items():  # host orderings (input preparation, not timed above)
+        t0 = time.perf_counter()
+        orders[name] = make()
+        host_s[name] = round(time.perf_counter() - t0, 3)
     import torch
     ch = tl.CountHash(stream.cuda_stream)
     g = tl.tl_graph_load(n, e_dev, stream.cuda_stream)
@@ -624,7 +633,8 @@ def ordering_sweep(tl, n, e, e_dev, stream):
                 tl.tl_list_triangles(g, a, CHUNK_BYTES, tl.tl_count_hash_ptr(), ch.user)
                 st = tl.tl_last_list_stats(g)
                 rows.append({"ordering": name, "alg": an, "cost": tl.tl_cost(g, a),
-                             "list_kernel_ms": sum(st["kernel_ms"]), "triangles": st["triangles"]})
+                             "list_kernel_ms": sum(st["kernel_ms"]), "triangles": st["triangles"],
+                             "host_ordering_s": host_s[name]})
     finally:
         tl.tl_graph_free(g)
         ch.release()

@@ -8,7 +8,10 @@
  *  - order_core:  degeneracy ordering by the bucket peeling of Batagelj and
  *                 Zaversnik (2003), which Sec. 1.3 names for core ordering.
  *  - order_check: the Check heuristic of Sec. 3.3.2.
- *  - order_neigh: the Neigh heuristic of Sec. 3.3.1 (Algorithm 3, Fig. 3).
+ *  - order_neigh: the Neigh heuristic of Sec. 3.3.1 (Algorithm 3, Fig. 3),
+ *                 minimising C+- as in the paper or C++ = sum of d+^2 (Sec.
+ *                 3.3.1 notes that the heuristic serves other objectives,
+ *                 C++ among them).
  *
  * Plain C99; no platform-specific code.
  */
@@ -148,22 +151,54 @@ static int cmp_by_key(const void *a, const void *b) {
   return (ka > kb) - (ka < kb);
 }
 
-static int64_t cost_pm(int64_t n, const int64_t *dp, const int64_t *dm) {
+/* The cost Neigh minimises (Sec. 3.1): C+- = sum d+ d- (objective 0) or
+ * C++ = sum d+^2 (objective 1). */
+static int64_t neigh_cost(int64_t objective, int64_t n, const int64_t *dp, const int64_t *dm) {
   int64_t c = 0;
-  for (int64_t v = 0; v < n; ++v) c += dp[v] * dm[v];
+  for (int64_t v = 0; v < n; ++v) c += objective ? dp[v] * dp[v] : dp[v] * dm[v];
   return c;
+}
+
+/* Best slot of a vertex u of degree d whose neighbours nb[0..d) are sorted
+ * in the current order, the first pcur of them before u.  Slot p puts u just
+ * after nb[p-1] (p = 0: before nb[0]): u gets d- = p and d+ = d - p, and a
+ * neighbour nb[j] has u as a successor iff j < p.  With dp'/dm' a
+ * neighbour's degrees without its edge to u, the cost at slot p is a
+ * constant plus
+ *   C+-: p (d - p) + sum_{j<p} (dm'_j - dp'_j)
+ *   C++: (d - p)^2 + sum_{j<p} (2 dp'_j + 1)     [(dp' + 1)^2 - dp'^2]
+ * Among slots of equal cost the current one is kept, else the smallest p. */
+static int64_t neigh_best_slot(int64_t objective, int64_t d, const uint32_t *nb, int64_t pcur,
+                               const int64_t *dp, const int64_t *dm) {
+  int64_t best_p = pcur, best = 0, cur_val = 0, run = 0;
+  int have = 0;
+  for (int64_t p = 0; p <= d; ++p) {
+    int64_t val = (objective ? (d - p) * (d - p) : p * (d - p)) + run;
+    if (p == pcur) cur_val = val;
+    if (!have || val < best) best = val, best_p = p, have = 1;
+    if (p < d) {
+      uint32_t v = nb[p];
+      int64_t before = p < pcur; /* v currently precedes u */
+      int64_t dpv = dp[v] - before;
+      int64_t dmv = dm[v] - (1 - before);
+      run += objective ? 2 * dpv + 1 : dmv - dpv;
+    }
+  }
+  return cur_val <= best ? pcur : best_p;
 }
 
 /* Neigh: starting from `rank` (updated in place), repeat passes over the
  * vertices in increasing id; each vertex u moves to the slot p* in [0, d_u]
  * (just after its p*-th neighbour in the current order, or before all of
- * them for p* = 0) that minimises C+-.  A pass is repeated while it cut
- * C+- by more than a factor (1 - eps) (stopping rule of Algorithm 3; Neigh
- * stops after `max_iter` passes at most).  Among equal costs the current
- * slot is kept, else the smallest p.  Returns the number of passes. */
+ * them for p* = 0) that minimises the cost (C+- for objective 0, C++ for
+ * objective 1).  A pass is repeated while it cut the cost by more than a
+ * factor (1 - eps) (stopping rule of Algorithm 3; Neigh stops after
+ * `max_iter` passes at most).  Among equal costs the current slot is kept,
+ * else the smallest p.  cost_trace[i] = the cost before pass i and after
+ * the last one.  Returns the number of passes. */
 int64_t tls_order_neigh(int64_t n, const int64_t *off, const uint32_t *adj,
                         uint32_t *rank, double eps, int64_t max_iter,
-                        int64_t *cost_trace) {
+                        int64_t *cost_trace, int64_t objective) {
   olist L;
   L.n = n;
   L.prev = (int64_t *)malloc(sizeof(int64_t) * n);
@@ -195,7 +230,7 @@ int64_t tls_order_neigh(int64_t n, const int64_t *off, const uint32_t *adj,
   int64_t iters = 0;
   g_sort_key = L.key;
   while (iters < max_iter) {
-    int64_t c0 = cost_pm(n, dp, dm);
+    int64_t c0 = neigh_cost(objective, n, dp, dm);
     if (cost_trace) cost_trace[iters] = c0;
     for (int64_t u = 0; u < n; ++u) {
       int64_t d = off[u + 1] - off[u];
@@ -205,23 +240,7 @@ int64_t tls_order_neigh(int64_t n, const int64_t *off, const uint32_t *adj,
       /* current slot of u = number of neighbours before it */
       int64_t pcur = 0;
       while (pcur < d && L.key[nb[pcur]] < L.key[u]) ++pcur;
-      /* cost(p) - const = p (d - p) + sum_{j < p} (dm'_j - dp'_j), where
-       * dp'/dm' are the neighbour's degrees without its edge to u. */
-      int64_t best_p = pcur, run = 0, best = 0, cur_val = 0;
-      int have = 0;
-      for (int64_t p = 0; p <= d; ++p) {
-        int64_t val = p * (d - p) + run;
-        if (p == pcur) cur_val = val;
-        if (!have || val < best) best = val, best_p = p, have = 1;
-        if (p < d) {
-          uint32_t v = nb[p];
-          int64_t before = L.key[v] < L.key[u];  /* v currently a predecessor of u */
-          int64_t dpv = dp[v] - (before ? 1 : 0);
-          int64_t dmv = dm[v] - (before ? 0 : 1);
-          run += dmv - dpv;
-        }
-      }
-      if (cur_val <= best) best_p = pcur;
+      int64_t best_p = neigh_best_slot(objective, d, nb, pcur, dp, dm);
       if (best_p == pcur) continue;
       /* update degrees: neighbours before slot best_p are predecessors */
       for (int64_t j = 0; j < d; ++j) {
@@ -239,10 +258,10 @@ int64_t tls_order_neigh(int64_t n, const int64_t *off, const uint32_t *adj,
       else ol_insert_after(&L, u, nb[best_p - 1]);
     }
     ++iters;
-    int64_t c1 = cost_pm(n, dp, dm);
+    int64_t c1 = neigh_cost(objective, n, dp, dm);
     if (!((double)c1 < (1.0 - eps) * (double)c0)) break;
   }
-  if (cost_trace) cost_trace[iters] = cost_pm(n, dp, dm);
+  if (cost_trace) cost_trace[iters] = neigh_cost(objective, n, dp, dm);
   int64_t i = 0;
   for (int64_t v = L.head; v >= 0; v = L.next[v]) rank[v] = (uint32_t)i++;
   free(nb);
@@ -256,7 +275,7 @@ int64_t tls_order_neigh(int64_t n, const int64_t *off, const uint32_t *adj,
 
 /* Single Neigh move of one vertex (the update of Fig. 3), for tests. */
 void tls_neigh_move_one(int64_t n, const int64_t *off, const uint32_t *adj,
-                        uint32_t *rank, int64_t u) {
+                        uint32_t *rank, int64_t u, int64_t objective) {
   (void)n;
   /* Build the same state as order_neigh, run the body for u only. */
   int64_t d = off[u + 1] - off[u];
@@ -278,19 +297,7 @@ void tls_neigh_move_one(int64_t n, const int64_t *off, const uint32_t *adj,
   }
   int64_t pcur = 0;
   while (pcur < d && rank[nb[pcur]] < rank[u]) ++pcur;
-  int64_t best_p = pcur, run = 0, best = 0, cur_val = 0;
-  int have = 0;
-  for (int64_t p = 0; p <= d; ++p) {
-    int64_t val = p * (d - p) + run;
-    if (p == pcur) cur_val = val;
-    if (!have || val < best) best = val, best_p = p, have = 1;
-    if (p < d) {
-      uint32_t v = nb[p];
-      int64_t before = rank[v] < rank[u];
-      run += (dm[v] - (before ? 0 : 1)) - (dp[v] - (before ? 1 : 0));
-    }
-  }
-  if (cur_val <= best) best_p = pcur;
+  int64_t best_p = neigh_best_slot(objective, d, nb, pcur, dp, dm);
   if (best_p != pcur) {
     /* new position: just after neighbour best_p-1, or just before nb[0] */
     uint32_t old = rank[u];

@@ -48,9 +48,9 @@ def _helper():
             lib.tls_order_core.restype = I64
             lib.tls_order_check.argtypes = [I64, P, P, P, P]
             lib.tls_order_check.restype = None
-            lib.tls_order_neigh.argtypes = [I64, P, P, P, ctypes.c_double, I64, P]
+            lib.tls_order_neigh.argtypes = [I64, P, P, P, ctypes.c_double, I64, P, I64]
             lib.tls_order_neigh.restype = I64
-            lib.tls_neigh_move_one.argtypes = [I64, P, P, P, I64]
+            lib.tls_neigh_move_one.argtypes = [I64, P, P, P, I64, I64]
             lib.tls_neigh_move_one.restype = None
             _lib = lib
     return _lib
@@ -169,27 +169,37 @@ def order_check(off: np.ndarray, adj: np.ndarray, order: np.ndarray | None = Non
     return rank
 
 
+_OBJECTIVES = {"C+-": 0, "C++": 1}
+
+
 def order_neigh(off: np.ndarray, adj: np.ndarray, start: np.ndarray | None = None,
-                eps: float = 1e-2, max_iter: int = 50) -> tuple[np.ndarray, list[int]]:
+                eps: float = 1e-2, max_iter: int = 50,
+                objective: str = "C+-") -> tuple[np.ndarray, list[int]]:
     """Neigh heuristic (Algorithm 3), epsilon = 1e-2 as in Sec. 3.3.1.
 
-    Starts from ``start`` (default: the degree ordering).  Returns the rank
-    array and the C+- value before each pass and after the last one.
+    Minimises ``objective``: "C+-" (the paper's), or "C++" (the same local
+    moves for the cost of Algorithm 1; Sec. 3.3.1 notes that the heuristic
+    serves other objectives, C++ among them).  Starts from ``start`` (default: the degree
+    ordering).  Returns the rank array and the objective before each pass and
+    after the last one.
     """
+    obj = _OBJECTIVES[objective]
     n = off.shape[0] - 1
     rank = np.array(order_degree(off) if start is None else start, dtype=np.uint32)
     off = np.ascontiguousarray(off, dtype=np.int64)
     adj = np.ascontiguousarray(adj, dtype=np.uint32)
     trace = np.zeros(max_iter + 1, dtype=np.int64)
-    it = _helper().tls_order_neigh(n, _p(off), _p(adj), _p(rank), eps, max_iter, _p(trace))
+    it = _helper().tls_order_neigh(n, _p(off), _p(adj), _p(rank), eps, max_iter, _p(trace), obj)
     return rank, [int(x) for x in trace[: it + 1]]
 
 
-def neigh_move_one(off: np.ndarray, adj: np.ndarray, rank: np.ndarray, u: int) -> np.ndarray:
+def neigh_move_one(off: np.ndarray, adj: np.ndarray, rank: np.ndarray, u: int,
+                   objective: str = "C+-") -> np.ndarray:
     """One Neigh update of vertex ``u`` (the move shown in Fig. 3)."""
+    obj = _OBJECTIVES[objective]
     n = off.shape[0] - 1
     r = np.array(rank, dtype=np.uint32)
     off = np.ascontiguousarray(off, dtype=np.int64)
     adj = np.ascontiguousarray(adj, dtype=np.uint32)
-    _helper().tls_neigh_move_one(n, _p(off), _p(adj), _p(r), int(u))
+    _helper().tls_neigh_move_one(n, _p(off), _p(adj), _p(r), int(u), obj)
     return r

@@ -36,6 +36,7 @@ def _orderings(n, e, which=("identity", "random", "degree", "core", "split", "ch
         "split": lambda: synth.order_split(off),
         "check": lambda: synth.order_check(off, adj),
         "neigh": lambda: synth.order_neigh(off, adj)[0],
+        "neigh_c++": lambda: synth.order_neigh(off, adj, objective="C++")[0],
     }
     for name in which:
         yield name, table[name]()
@@ -126,7 +127,8 @@ def test_config1_chung_lu_full_set():
     ordering, A++ (plus A+- and other orderings): full set compare."""
     n = 10000
     e = synth.chung_lu(n, 20, 2.5, 1)
-    _compare(n, e, _orderings(n, e, ("degree", "core", "random", "split", "check", "neigh")))
+    _compare(n, e, _orderings(n, e, ("degree", "core", "random", "split", "check", "neigh",
+                                     "neigh_c++")))
 
 
 def test_host_edges_and_host_rank():

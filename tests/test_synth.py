@@ -109,3 +109,75 @@ def test_device_generator_matches_host_generator():
     assert np.array_equal(e, t.numpy().view(np.uint32))
     assert np.array_equal(synth.counter_uniform(3, 1, 1000, start=77),
                           dev.counter_uniform_t(3, 1, 1000, 77, "cpu").numpy())
+
+
+def _place(rank, u, nb_sorted, p):
+    """Ordering with u removed and put back just after nb_sorted[p-1]
+    (p = 0: just before nb_sorted[0]); rank order of the others unchanged."""
+    seq = [v for v in np.argsort(rank, kind="stable") if v != u]
+    at = seq.index(nb_sorted[0]) if p == 0 else seq.index(nb_sorted[p - 1]) + 1
+    seq.insert(at, u)
+    out = np.empty(len(rank), dtype=np.uint32)
+    out[np.array(seq)] = np.arange(len(rank), dtype=np.uint32)
+    return out
+
+
+@pytest.mark.parametrize("objective,alg", [("C+-", oracle.APM), ("C++", oracle.APP)])
+def test_neigh_move_takes_the_cheapest_slot(objective, alg):
+    """One Neigh move (Algorithm 3) against brute force: every slot of the
+    moved vertex among its neighbours is tried and its cost computed by the
+    oracle; the move lands on a cheapest one, the current slot on a tie, else
+    the smallest."""
+    rng = np.random.default_rng(11)
+    moved = 0
+    for trial in range(12):
+        n = 14
+        e = np.array([(a, b) for a in range(n) for b in range(a + 1, n) if rng.random() < 0.35],
+                     dtype=np.uint32)
+        off, adj = synth.simple_csr(n, e)
+        g = oracle.Graph(n, e)
+        rank = rng.permutation(n).astype(np.uint32)
+        for u in range(n):
+            nb = adj[off[u]:off[u + 1]]
+            if len(nb) == 0:
+                continue
+            nb_sorted = sorted(nb, key=lambda v: rank[v])
+            pcur = sum(rank[v] < rank[u] for v in nb)
+            costs = []
+            for p in range(len(nb) + 1):
+                g.order_apply(_place(rank, u, nb_sorted, p))
+                costs.append(g.cost(alg))
+            best = min(costs)
+            want_p = pcur if costs[pcur] == best else costs.index(best)
+            got = synth.orderings.neigh_move_one(off, adj, rank, u, objective)
+            g.order_apply(got)
+            assert g.cost(alg) == best
+            assert np.array_equal(got, rank if want_p == pcur else _place(rank, u, nb_sorted, want_p))
+            moved += want_p != pcur
+    assert moved > 20
+
+
+def test_neigh_for_cpp_lowers_cpp_and_reaches_the_star_bound():
+    n = 3000
+    e = synth.chung_lu(n, 16, 2.3, 8)
+    off, adj = synth.simple_csr(n, e)
+    g = oracle.Graph(n, e)
+    g.order_apply(synth.order_degree(off))
+    c_deg = g.cost(oracle.APP)
+    rank, trace = synth.order_neigh(off, adj, objective="C++")
+    assert np.array_equal(np.sort(rank), np.arange(n))
+    assert trace[0] == c_deg
+    assert all(b <= a for a, b in zip(trace, trace[1:]))
+    g.order_apply(rank)
+    assert g.cost(oracle.APP) == trace[-1] < c_deg
+    # a star with its hub first has C++ = (n-1)^2; every edge adds at least
+    # one to C++ (C++ >= m), and Neigh brings it down to that bound
+    k = 200
+    star = np.array([(0, v) for v in range(1, k)], dtype=np.uint32)
+    off, adj = synth.simple_csr(k, star)
+    hub_first = np.arange(k, dtype=np.uint32)
+    rank, trace = synth.order_neigh(off, adj, start=hub_first, objective="C++")
+    assert trace[0] == (k - 1) ** 2 and trace[-1] == k - 1
+    g = oracle.Graph(k, star)
+    g.order_apply(rank)
+    assert g.cost(oracle.APP) == k - 1
