@@ -590,7 +590,7 @@ def run_tl(args):
                     "d2h_bytes_per_step": 2 * 16},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_list_small + k_list_large (A++ and A+-)",
+                         "kernel": "k_list_warp<64|2048> + k_list_cta<256,2|1024,3> (A++ and A+-)",
                          "algorithmic_bytes_per_step": alg_bytes, "kernel_ms_per_step": list_ms,
                          "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"},
             "list_stats": {a: r[3] for a, r in zip(("A++", "A+-"), out)},
@@ -712,7 +712,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tl", choices=["tl", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")

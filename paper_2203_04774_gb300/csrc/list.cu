@@ -402,29 +402,34 @@ __device__ __forceinline__ void scan_items(const ListArgs &a, uint64_t pb, uint6
     }
     const uint64_t Ej0 = shfl_u64(E, j0);
     if (Ej0 - base >= 32) {
-      // Long run: every test up to min(Ej0, i1) scans the same list N+_y.
+      // Long run: every test up to min(Ej0, i1) scans the same list N+_y (at
+      // most 2^31 tests per run, so that offsets within it fit 32 bits).
       const uint64_t Aj = shfl_u64(A, j0) + base;
       const uint32_t iyj = __shfl_sync(0xffffffffu, iy, j0);
-      const uint64_t run = (Ej0 < i1 ? Ej0 : i1) - base;
+      const uint64_t rest = (Ej0 < i1 ? Ej0 : i1) - base;
+      const uint32_t run = rest < (1ull << 31) ? (uint32_t)rest : (1u << 31);
       // Each lane takes 4 consecutive elements with one aligned 16-byte load
-      // (scan_adj is 256-byte aligned and padded by 4 elements; elements
-      // outside [lo, hi) are masked), and the warp reserves slab room for the
-      // 128 tests of an iteration at once.
-      const uint64_t lo = Aj, hi = Aj + run;
-      for (uint64_t q0 = lo & ~3ull; q0 < hi; q0 += 128) {
+      // (scan_adj is 256-byte aligned and padded by 4 elements), and the warp
+      // reserves slab room for the 128 tests of an iteration at once.  Offsets
+      // count from the aligned element before the run's first test, which
+      // sits `lead` elements in: element e is a test of the run iff
+      // lead <= e < lead + run.
+      const uint32_t *src = a.scan_adj + (Aj & ~3ull);
+      const uint32_t lead = (uint32_t)(Aj & 3), span = lead + run;
+      for (uint32_t e0 = 0; e0 < span; e0 += 128) {
         if (kEmit == 1 && o.cnt > kWarpBuf - kWarpStep) {
           // every test before this iteration's first one has its hits in buf
-          if (!warp_commit(a, o, inv_x, base + (q0 > lo ? q0 - lo : 0), probes)) return;
+          // (and is counted in lane 0's probes)
+          if (!warp_commit(a, o, inv_x, base + (e0 > lead ? e0 - lead : 0), probes)) return;
         }
-        const uint64_t q = q0 + 4 * lane;
+        const uint32_t e = e0 + 4 * lane;
         uint4 v = make_uint4(0, 0, 0, 0);
-        if (q < hi) v = *reinterpret_cast<const uint4 *>(a.scan_adj + q);
+        if (e < span) v = *reinterpret_cast<const uint4 *>(src + e);
         const uint32_t z[4] = {v.x, v.y, v.z, v.w};
-        // the iteration's tests: [max(q0, lo), min(q0 + 128, hi)), counted once
-        if (lane == 0) probes += (q0 + 128 < hi ? q0 + 128 : hi) - (q0 > lo ? q0 : lo);
+        if (lane == 0) probes += (e0 + 128 < span ? e0 + 128 : span) - (e0 > lead ? e0 : lead);
         bool hit[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) hit[u] = q + u >= lo && q + u < hi && member(z[u]);
+        for (int u = 0; u < 4; ++u) hit[u] = e + u - lead < run && member(z[u]);
         // positions: the hits of element u of all lanes, u = 0..3, one after
         // the other (the order of triangles is free)
         unsigned hm[4];
