@@ -70,13 +70,31 @@ __device__ __forceinline__ uint64_t shfl_u64(uint64_t v, int src) {
   return ((uint64_t)hi << 32) | lo;
 }
 
-__device__ __forceinline__ uint64_t upper_bound_u64(const uint64_t *v, uint64_t n, uint64_t key) {
-  uint64_t lo = 0, hi = n;
-  while (lo < hi) {
-    uint64_t mid = (lo + hi) >> 1;
-    if (v[mid] <= key) lo = mid + 1; else hi = mid;
+// Number of elements <= key in the sorted v[0, n), by the whole warp (every
+// lane calls it with the same arguments and gets the result): each round the
+// lanes sample 32 evenly spaced elements and one ballot narrows the range
+// 32-fold, so a search takes about log32(n) + 1 dependent loads instead of
+// log2(n).  Invariant: every element before `base` is <= key and the count
+// lies in [base, base + cnt].
+__device__ __forceinline__ uint64_t warp_upper_bound_u64(const uint64_t *v, uint64_t n,
+                                                         uint64_t key) {
+  const int lane = threadIdx.x & 31;
+  uint64_t base = 0, cnt = n;
+  while (cnt > 32) {
+    const uint64_t step = (cnt + 31) >> 5;  // 32 step >= cnt
+    const uint64_t idx = base + (uint64_t)lane * step;
+    const bool le = idx < base + cnt && v[idx] <= key;
+    const uint32_t c = __popc(__ballot_sync(0xffffffffu, le));  // samples <= key: a prefix
+    if (c == 0) return base;
+    // sample c-1 is <= key; sample c (if any) is > key or past the range
+    const uint64_t lo = base + (uint64_t)(c - 1) * step + 1;
+    const uint64_t hi = base + (uint64_t)c * step < base + cnt ? base + (uint64_t)c * step
+                                                               : base + cnt;
+    base = lo;
+    cnt = hi - lo;
   }
-  return lo;
+  const bool le = (uint64_t)lane < cnt && v[base + lane] <= key;
+  return base + __popc(__ballot_sync(0xffffffffu, le));
 }
 
 __device__ __forceinline__ uint64_t lower_bound_u64(const uint64_t *v, uint64_t n, uint64_t key) {
@@ -348,7 +366,7 @@ __device__ __forceinline__ void scan_items(const ListArgs &a, uint64_t pb, uint6
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   // seed edge holding test i0
-  uint64_t k = (k0 != ~0ull) ? k0 : pb + upper_bound_u64(a.WP + pb, pe - pb, i0) - 1;
+  uint64_t k = (k0 != ~0ull) ? k0 : pb + warp_upper_bound_u64(a.WP + pb, pe - pb, i0) - 1;
   uint64_t E = 0, A = 0, Elast = 0;
   uint32_t iy = 0;
   auto load_window = [&](uint64_t kw) {
