@@ -332,7 +332,8 @@ TL_EXPORT tl_status tl_server_add_ordering(tl_server *s, uint32_t graph_id, cons
 TL_EXPORT tl_status tl_server_submit(tl_server *s, uint32_t graph_id, uint32_t ordering_id,
                                      tl_alg alg, uint64_t *request_id);
 /* Block until the request has finished and return its result (each id can
- * be waited for once).  An unknown id -> TL_EINVAL. */
+ * be waited for once, by one thread).  An unknown id, or an id another
+ * thread is already waiting for -> TL_EINVAL. */
 TL_EXPORT tl_status tl_server_wait(tl_server *s, uint64_t request_id, tl_request_result *out);
 /* Finish every submitted request, stop the workers, release the server's
  * device memory.  NULL is a no-op. */

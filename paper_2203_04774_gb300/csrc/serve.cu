@@ -35,6 +35,7 @@ struct Request {
   tl_alg alg = TL_APP;
   uint64_t footprint = 0;
   bool done = false;
+  bool waited = false;  // a thread is waiting for it (at most one may)
   tl_request_result res{};
 };
 
@@ -348,6 +349,8 @@ tl_status tl_server_wait(tl_server *S, uint64_t request_id, tl_request_result *o
   auto it = S->requests.find(request_id);
   if (it == S->requests.end()) tl::fail(TL_EINVAL, "unknown request id");
   Request *r = it->second;
+  if (r->waited) tl::fail(TL_EINVAL, "another thread is already waiting for this request");
+  r->waited = true;
   S->cv_done.wait(lk, [r] { return r->done; });
   *out = r->res;
   S->requests.erase(it);

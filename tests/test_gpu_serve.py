@@ -160,3 +160,30 @@ def test_server_argument_errors(pool):
     r = srv.wait(srv.submit(gid, oid, tl.TL_APP))
     assert (r["triangles"], r["hash"]) == pool[0][3][(0, tl.TL_APP)]
     srv.close()
+
+
+def test_one_waiter_per_request(pool):
+    """Two threads wait for the same request: one gets its result, the other
+    TL_EINVAL (the id is either being waited for or already consumed)."""
+    srv = tl.Server(8 << 30, max_batch=4, workers=1)
+    n, e, orders, want = pool[-1]
+    g = tl.Graph(n, _dev(e))
+    gid = srv.add_graph(g)
+    oid = srv.add_ordering(gid, _dev(orders[0]))
+    rid = srv.submit(gid, oid, tl.TL_APM)
+    got, errs = [], []
+
+    def waiter():
+        try:
+            got.append(srv.wait(rid))
+        except tl.TLError as ex:
+            errs.append(ex.status)
+
+    threads = [threading.Thread(target=waiter) for _ in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert errs == [tl.TL_EINVAL] and len(got) == 1
+    assert (got[0]["triangles"], got[0]["hash"]) == want[(0, tl.TL_APM)]
+    srv.close()
