@@ -17,6 +17,8 @@
 // a list of at least 32 tests is streamed with 16-byte loads, shorter ones
 // share 32-test steps in which each lane finds its seed edge by a shuffle
 // binary search over the window, so all lanes work whatever the lengths.
+// The seed edge of a range's first test is found by the whole warp (32
+// samples of WP and a ballot per round).
 //
 // B (the boolean array of the algorithms) per tier:
 //   small/medium x: a per-warp hash table in shared memory (load <= 1/2), one
