@@ -13,10 +13,12 @@
  *                      Sec. 1.3, stored as a rank-space CSR of sorted
  *                      successor lists N+ and predecessor lists N-.
  *   tl_cost            C++(pi) = sum d+_u d+_u or C+-(pi) = sum d+_u d-_u
- *                      (Definition "Cost induced by an ordering", Sec. 3.1).
- *   tl_list_triangles  Algorithm 1 (A++) or Algorithm 2 (A+-) of Sec. 2.1;
- *                      each triangle is reported exactly once, in chunks of
- *                      device memory handed to a consumer callback.
+ *                      (Definition "Cost induced by an ordering", Sec. 3.1),
+ *                      or C-- = sum d-_u d-_u of the third variant.
+ *   tl_list_triangles  Algorithm 1 (A++), Algorithm 2 (A+-) or the third
+ *                      variant A-- of Sec. 2.1; each triangle is reported
+ *                      exactly once, in chunks of device memory handed to a
+ *                      consumer callback.
  *
  * Conventions common to every call
  *   - Every call returns a tl_status; no C++ exception crosses the ABI.
@@ -100,7 +102,7 @@ TL_EXPORT tl_status tl_graph_load(tl_graph **out, uint32_t n, const uint32_t *ed
  * Cleaning as in tl_graph_load; the ordering starts as the identity.
  * On a union (from either call) tl_order_compute works part by part: part
  * i's vertices get the ranks vbase_i + (their ranks in the part's own
- * degree or Split ordering), so ranks [vbase_i, vbase_{i+1}) are part i's
+ * degree, Split or core ordering), so ranks [vbase_i, vbase_{i+1}) are part i's
  * and a tl_list_triangles_range over them lists part i alone. */
 TL_EXPORT tl_status tl_graph_load_parts(tl_graph **out, uint32_t k, const uint32_t *n,
                                         const uint64_t *m_in, const uint32_t *edges,
