@@ -626,6 +626,19 @@ def ordering_sweep(tl, n, e, e_dev, stream):
     g = tl.tl_graph_load(n, e_dev, stream.cuda_stream)
     rows = []
     try:
+        # the device orderings (the ordering step of the full-listing task),
+        # CUDA events on the handle's stream, after one warm-up call each
+        dev_ms = {}
+        rk = torch.empty(n, dtype=torch.int32, device="cuda")
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        for name, kind in (("degree", tl.TL_ORDER_DEGREE), ("split", tl.TL_ORDER_SPLIT),
+                           ("core", tl.TL_ORDER_CORE)):
+            tl.tl_order_compute(g, kind, rk)
+            ev[0].record(stream)
+            tl.tl_order_compute(g, kind, rk)
+            ev[1].record(stream)
+            ev[1].synchronize()
+            dev_ms[name] = round(ev[0].elapsed_time(ev[1]), 3)
         for name, r in orders.items():
             tl.tl_order_apply(g, torch.from_numpy(r).cuda())
             for a, an in ((tl.TL_APP, "A++"), (tl.TL_APM, "A+-"), (tl.TL_AMM, "A--")):
@@ -638,9 +651,10 @@ def ordering_sweep(tl, n, e, e_dev, stream):
     finally:
         tl.tl_graph_free(g)
         ch.release()
+    rows.append({"device_ordering_ms": dev_ms})
     for an in ("A++", "A+-", "A--"):
-        xs = [r["cost"] for r in rows if r["alg"] == an]
-        ys = [r["list_kernel_ms"] for r in rows if r["alg"] == an]
+        xs = [r["cost"] for r in rows if r.get("alg") == an]
+        ys = [r["list_kernel_ms"] for r in rows if r.get("alg") == an]
         if len(xs) > 2 and np.std(xs) > 0 and np.std(ys) > 0:
             rows.append({"alg": an, "pearson_r_cost_vs_time": float(np.corrcoef(xs, ys)[0, 1])})
     return rows
