@@ -93,3 +93,21 @@ def test_two_gloo_ranks_combine_to_the_full_listing():
         want = [c, int(np.uint64(h).astype(np.int64)), p, g.cost(alg)]
         assert out[0][alg] == want and out[1][alg] == want
         assert shard.combine([(c, h)]) == (c, h)
+
+
+def test_balanced_ranges_edge_cases():
+    # more parts than vertices, all-zero work, one heavy vertex: still a
+    # partition of [0, n) into contiguous (possibly empty) ranges
+    for work in (np.zeros(5, np.int64), np.array([0, 0, 100, 0], np.int64),
+                 np.ones(3, np.int64), np.zeros(0, np.int64)):
+        n = len(work)
+        for parts in (1, 2, 7):
+            rg = shard.balanced_ranges(work, parts)
+            assert len(rg) == parts and rg[0][0] == 0 and rg[-1][1] == n
+            assert all(b <= e for b, e in rg)
+            assert all(rg[i][1] == rg[i + 1][0] for i in range(parts - 1))
+            assert sum(int(work[b:e].sum()) for b, e in rg) == int(work.sum())
+    with pytest.raises(ValueError):
+        shard.balanced_ranges(np.ones(4), 0)
+    # the combine wraps the hash sum mod 2^64
+    assert shard.combine([(1, (1 << 64) - 1), (2, 5)]) == (3, 4)
