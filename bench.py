@@ -594,6 +594,7 @@ def run_tl(args):
                          "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                          "kernel": "k_list_warp<64|2048> + k_list_cta<256,2|1024,3> (A++ and A+-)",
                          "algorithmic_bytes_per_step": alg_bytes, "kernel_ms_per_step": list_ms,
+                         "compulsory_bytes_per_step": len(costs) * (8 * m + 12 * T),
                          "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"},
             "list_stats": {a: r[3] for a, r in zip(("A++", "A+-"), out)},
             "phase_ms_median": timed_phase_ms,
