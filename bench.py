@@ -405,16 +405,20 @@ class Clocks:
         self.gpu = gpu_index
         self.proc = None
         self.path = None
+        self.out = None
 
     def start(self):
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
+            self.out = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "200"], stdout=self.out, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            if self.out:
+                self.out.close()
 
     def stop(self):
         if not self.proc:
@@ -424,6 +428,7 @@ class Clocks:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
+        self.out.close()
         rows = []
         with open(self.path) as f:
             for line in f:
