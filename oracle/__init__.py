@@ -60,6 +60,8 @@ def _load():
             lib.or_list.restype = I
             lib.or_csr.argtypes = [P, I, P, P]
             lib.or_csr.restype = I
+            lib.or_degrees.argtypes = [P, P]
+            lib.or_degrees.restype = I
             lib.or_hash_triples.argtypes = [P, U64]
             lib.or_hash_triples.restype = U64
             lib.or_mix64.argtypes = [U64]
@@ -134,6 +136,12 @@ class Graph:
         if st != 0:
             raise OracleError(f"or_list status {st}")
         return None, int(cnt.value), int(hsh.value), int(prb.value)
+
+    def degrees(self) -> np.ndarray:
+        """Degree of every vertex of the cleaned simple graph (Sec. 1.3)."""
+        deg = np.empty(self.n, dtype=np.uint32)
+        _lib.or_degrees(self._h, _ptr(deg))
+        return deg
 
     def csr(self, direction: int):
         """(off uint64[n+1], adj uint32[m]) of N+ (0) or N- (1), rank space."""

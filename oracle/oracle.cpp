@@ -32,6 +32,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <utility>
 #include <vector>
 
@@ -58,9 +59,31 @@ struct Graph {
   // Ordering and the DAG G_pi in rank space (Sec. 1.3).
   std::vector<uint32_t> rank;  // rank[v] = pi_v - 1
   std::vector<uint32_t> inv;   // inv[rank[v]] = v
-  std::vector<std::vector<uint32_t>> out;  // N+_x: successors of rank x, ascending
-  std::vector<std::vector<uint32_t>> in;   // N-_x: predecessors of rank x, ascending
+  // N+_x (successors of rank x) = out_adj[out_off[x] .. out_off[x+1]),
+  // N-_x (predecessors) = in_adj[in_off[x] .. in_off[x+1]), each ascending.
+  // Exact-size arrays, so that a graph of 2e9 edges fits in host memory.
+  std::vector<uint64_t> out_off, in_off;
+  std::vector<uint32_t> out_adj, in_adj;
+  // The DAG is built on first use (so that loading a large graph and then
+  // applying an ordering builds it once); the mutex guards that build.
+  bool dag_ready = false;
+  std::mutex dag_mu;
 };
+
+// A neighbour list as a range of ranks, for range-for loops.
+struct Row {
+  const uint32_t *b, *e;
+  const uint32_t *begin() const { return b; }
+  const uint32_t *end() const { return e; }
+  uint64_t size() const { return uint64_t(e - b); }
+};
+
+Row Nplus(const Graph &g, uint32_t x) {
+  return Row{g.out_adj.data() + g.out_off[x], g.out_adj.data() + g.out_off[x + 1]};
+}
+Row Nminus(const Graph &g, uint32_t x) {
+  return Row{g.in_adj.data() + g.in_off[x], g.in_adj.data() + g.in_off[x + 1]};
+}
 
 // Where found triangles go: a buffer of triples (may be absent), a count and
 // the set hash.
@@ -86,18 +109,44 @@ struct Sink {
 };
 
 // Orient every edge of E by the ordering (Sec. 1.3): (u, v) in E_pi iff
-// pi_u < pi_v, stored as u -> v in rank space.
+// pi_u < pi_v, stored as u -> v in rank space.  The rows are sized by
+// counting d+ and d- first, filled, then sorted.
 void build_dag(Graph &g) {
-  g.out.assign(g.n, {});
-  g.in.assign(g.n, {});
+  const uint64_t m = g.E.size();
+  g.out_off.assign(uint64_t(g.n) + 1, 0);
+  g.in_off.assign(uint64_t(g.n) + 1, 0);
+  for (const auto &e : g.E) {
+    uint32_t ra = g.rank[e.first], rb = g.rank[e.second];
+    ++g.out_off[std::min(ra, rb) + 1];  // d+ of the lower rank
+    ++g.in_off[std::max(ra, rb) + 1];   // d- of the higher rank
+  }
+  for (uint32_t x = 0; x < g.n; ++x) {
+    g.out_off[x + 1] += g.out_off[x];
+    g.in_off[x + 1] += g.in_off[x];
+  }
+  g.out_adj.assign(m, 0);
+  g.in_adj.assign(m, 0);
+  std::vector<uint64_t> out_pos(g.out_off.begin(), g.out_off.end() - 1);
+  std::vector<uint64_t> in_pos(g.in_off.begin(), g.in_off.end() - 1);
   for (const auto &e : g.E) {
     uint32_t ra = g.rank[e.first], rb = g.rank[e.second];
     uint32_t lo = std::min(ra, rb), hi = std::max(ra, rb);
-    g.out[lo].push_back(hi);
-    g.in[hi].push_back(lo);
+    g.out_adj[out_pos[lo]++] = hi;
+    g.in_adj[in_pos[hi]++] = lo;
   }
-  for (auto &l : g.out) std::sort(l.begin(), l.end());
-  for (auto &l : g.in) std::sort(l.begin(), l.end());
+  for (uint32_t x = 0; x < g.n; ++x) {
+    std::sort(g.out_adj.begin() + g.out_off[x], g.out_adj.begin() + g.out_off[x + 1]);
+    std::sort(g.in_adj.begin() + g.in_off[x], g.in_adj.begin() + g.in_off[x + 1]);
+  }
+  g.dag_ready = true;
+}
+
+// The DAG of the current ordering, built if no call has needed it yet.
+const Graph &with_dag(const void *h) {
+  Graph *g = static_cast<Graph *>(const_cast<void *>(h));
+  std::lock_guard<std::mutex> lock(g->dag_mu);
+  if (!g->dag_ready) build_dag(*g);
+  return *g;
 }
 
 // Algorithm 1 (A++), literally: for each vertex w, mark N-_w in B; for every
@@ -107,14 +156,14 @@ void list_app_literal(const Graph &g, uint32_t w_begin, uint32_t w_end, Sink &s,
                       uint64_t &probes) {
   std::vector<char> B(g.n, 0);
   for (uint32_t w = w_begin; w < w_end; ++w) {
-    for (uint32_t v : g.in[w]) B[v] = 1;
-    for (uint32_t u : g.in[w]) {
-      for (uint32_t v : g.out[u]) {
+    for (uint32_t v : Nminus(g, w)) B[v] = 1;
+    for (uint32_t u : Nminus(g, w)) {
+      for (uint32_t v : Nplus(g, u)) {
         ++probes;
         if (B[v]) s.output(u, v, w);
       }
     }
-    for (uint32_t v : g.in[w]) B[v] = 0;
+    for (uint32_t v : Nminus(g, w)) B[v] = 0;
   }
 }
 
@@ -124,14 +173,14 @@ void list_apm_literal(const Graph &g, uint32_t u_begin, uint32_t u_end, Sink &s,
                       uint64_t &probes) {
   std::vector<char> B(g.n, 0);
   for (uint32_t u = u_begin; u < u_end; ++u) {
-    for (uint32_t w : g.out[u]) B[w] = 1;
-    for (uint32_t v : g.out[u]) {
-      for (uint32_t w : g.out[v]) {
+    for (uint32_t w : Nplus(g, u)) B[w] = 1;
+    for (uint32_t v : Nplus(g, u)) {
+      for (uint32_t w : Nplus(g, v)) {
         ++probes;
         if (B[w]) s.output(u, v, w);
       }
     }
-    for (uint32_t w : g.out[u]) B[w] = 0;
+    for (uint32_t w : Nplus(g, u)) B[w] = 0;
   }
 }
 
@@ -145,14 +194,14 @@ void list_amm_literal(const Graph &g, uint32_t v_begin, uint32_t v_end, Sink &s,
                       uint64_t &probes) {
   std::vector<char> B(g.n, 0);
   for (uint32_t v = v_begin; v < v_end; ++v) {
-    for (uint32_t u : g.in[v]) B[u] = 1;
-    for (uint32_t w : g.out[v]) {
-      for (uint32_t u : g.in[w]) {
+    for (uint32_t u : Nminus(g, v)) B[u] = 1;
+    for (uint32_t w : Nplus(g, v)) {
+      for (uint32_t u : Nminus(g, w)) {
         ++probes;
         if (B[u]) s.output(u, v, w);
       }
     }
-    for (uint32_t u : g.in[v]) B[u] = 0;
+    for (uint32_t u : Nminus(g, v)) B[u] = 0;
   }
 }
 
@@ -167,11 +216,11 @@ void list_app_sets(const Graph &g, uint32_t w_begin, uint32_t w_end, Sink &s,
                    uint64_t &probes) {
   std::vector<uint32_t> common;
   for (uint32_t w = w_begin; w < w_end; ++w) {
-    for (uint32_t u : g.in[w]) {
+    for (uint32_t u : Nminus(g, w)) {
       common.clear();
-      std::set_intersection(g.out[u].begin(), g.out[u].end(), g.in[w].begin(),
-                            g.in[w].end(), std::back_inserter(common));
-      probes += g.out[u].size();
+      std::set_intersection(Nplus(g, u).begin(), Nplus(g, u).end(), Nminus(g, w).begin(),
+                            Nminus(g, w).end(), std::back_inserter(common));
+      probes += Nplus(g, u).size();
       for (uint32_t v : common) s.output(u, v, w);
     }
   }
@@ -181,11 +230,11 @@ void list_apm_sets(const Graph &g, uint32_t u_begin, uint32_t u_end, Sink &s,
                    uint64_t &probes) {
   std::vector<uint32_t> common;
   for (uint32_t u = u_begin; u < u_end; ++u) {
-    for (uint32_t v : g.out[u]) {
+    for (uint32_t v : Nplus(g, u)) {
       common.clear();
-      std::set_intersection(g.out[u].begin(), g.out[u].end(), g.out[v].begin(),
-                            g.out[v].end(), std::back_inserter(common));
-      probes += g.out[v].size();
+      std::set_intersection(Nplus(g, u).begin(), Nplus(g, u).end(), Nplus(g, v).begin(),
+                            Nplus(g, v).end(), std::back_inserter(common));
+      probes += Nplus(g, v).size();
       for (uint32_t w : common) s.output(u, v, w);
     }
   }
@@ -195,11 +244,11 @@ void list_amm_sets(const Graph &g, uint32_t v_begin, uint32_t v_end, Sink &s,
                    uint64_t &probes) {
   std::vector<uint32_t> common;
   for (uint32_t v = v_begin; v < v_end; ++v) {
-    for (uint32_t w : g.out[v]) {
+    for (uint32_t w : Nplus(g, v)) {
       common.clear();
-      std::set_intersection(g.in[v].begin(), g.in[v].end(), g.in[w].begin(), g.in[w].end(),
-                            std::back_inserter(common));
-      probes += g.in[w].size();
+      std::set_intersection(Nminus(g, v).begin(), Nminus(g, v).end(), Nminus(g, w).begin(),
+                            Nminus(g, w).end(), std::back_inserter(common));
+      probes += Nminus(g, w).size();
       for (uint32_t u : common) s.output(u, v, w);
     }
   }
@@ -234,7 +283,6 @@ int or_graph_new(uint32_t n, const uint32_t *edges, uint64_t m_in, void **out) {
   g->rank.resize(n);
   g->inv.resize(n);
   for (uint32_t v = 0; v < n; ++v) g->rank[v] = g->inv[v] = v;
-  build_dag(*g);
   *out = g;
   return 0;
 }
@@ -256,6 +304,7 @@ int or_order_apply(void *h, const uint32_t *rank) {
     g->rank[v] = rank[v];
     g->inv[rank[v]] = v;
   }
+  std::lock_guard<std::mutex> lock(g->dag_mu);
   build_dag(*g);
   return 0;
 }
@@ -264,10 +313,10 @@ int or_order_apply(void *h, const uint32_t *rank) {
 //   alg 0: C++ = sum_u d+_u * d+_u      alg 1: C+- = sum_u d+_u * d-_u
 //   alg 2: C-- = sum_u d-_u * d-_u (A--, by the same counting as Property 1)
 uint64_t or_cost(const void *h, int alg) {
-  const Graph *g = static_cast<const Graph *>(h);
+  const Graph *g = &with_dag(h);
   uint64_t c = 0;
   for (uint32_t x = 0; x < g->n; ++x) {
-    uint64_t dp = g->out[x].size(), dm = g->in[x].size();
+    uint64_t dp = Nplus(*g, x).size(), dm = Nminus(*g, x).size();
     c += (alg == 0) ? dp * dp : (alg == 1 ? dp * dm : dm * dm);
   }
   return c;
@@ -277,12 +326,13 @@ uint64_t or_cost(const void *h, int alg) {
 // 2), in the literal boolean-array form (mode 0) or the set-intersection form
 // (mode 1).  The outer loop runs over ranks [seed_begin, seed_end) (pass 0
 // and n for the whole graph; a sub-range lists the triangles whose third
-// vertex (A++), first vertex (A+-) or middle vertex (A--) lies in it).  Triples go to buf[3*cap] when buf is
-// not null.
+// vertex (A++), first vertex (A+-) or middle vertex (A--) lies in it).
+// Triples go to buf[3*cap] when buf is not null.  Calls on one graph may run
+// concurrently from several threads (each has its own B and sink).
 int or_list(const void *h, int alg, int mode, uint32_t seed_begin, uint32_t seed_end,
             uint32_t *buf, uint64_t cap, uint64_t *count, uint64_t *hash,
             uint64_t *probes) {
-  const Graph *g = static_cast<const Graph *>(h);
+  const Graph *g = &with_dag(h);
   if (alg < 0 || alg > 2 || mode < 0 || mode > 1) return 1;
   if (seed_end > g->n || seed_begin > seed_end) return 1;
   Sink s;
@@ -305,14 +355,25 @@ int or_list(const void *h, int alg, int mode, uint32_t seed_begin, uint32_t seed
 // Export the DAG as CSR in rank space: dir 0 = N+ (out), dir 1 = N- (in).
 // off[n+1] and adj[m] are caller-owned.
 int or_csr(const void *h, int dir, uint64_t *off, uint32_t *adj) {
-  const Graph *g = static_cast<const Graph *>(h);
-  const auto &L = (dir == 0) ? g->out : g->in;
+  const Graph *g = &with_dag(h);
   uint64_t k = 0;
   for (uint32_t x = 0; x < g->n; ++x) {
     off[x] = k;
-    for (uint32_t y : L[x]) adj[k++] = y;
+    for (uint32_t y : (dir == 0 ? Nplus(*g, x) : Nminus(*g, x))) adj[k++] = y;
   }
   off[g->n] = k;
+  return 0;
+}
+
+// Degree of every vertex of the simple graph (Sec. 1.3: its number of
+// neighbours), counted over the cleaned edge set E, original ids.
+int or_degrees(const void *h, uint32_t *deg) {
+  const Graph *g = static_cast<const Graph *>(h);
+  for (uint32_t v = 0; v < g->n; ++v) deg[v] = 0;
+  for (const auto &e : g->E) {
+    ++deg[e.first];
+    ++deg[e.second];
+  }
   return 0;
 }
 

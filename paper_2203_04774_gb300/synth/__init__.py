@@ -78,15 +78,29 @@ def counter_uniform(seed: int, stream: int, count: int, start: int = 0) -> np.nd
 
 
 def _draw_from_cdf(cdf: np.ndarray, seed: int, stream: int, count: int,
-                   block: int = 1 << 24) -> np.ndarray:
+                   block: int = 1 << 24, threads: int = 1) -> np.ndarray:
+    """Inverse-CDF draws of indices: draw i is the first index whose cdf
+    exceeds uniform i of the stream.  Blocks are independent (the generator
+    is counter-based), so ``threads`` > 1 draws them concurrently with the
+    same result."""
     n = cdf.shape[0]
     out = np.empty(count, dtype=np.uint32)
-    for s in range(0, count, block):
+
+    def one(s):
         c = min(block, count - s)
         u = counter_uniform(seed, stream, c, start=s)
         idx = np.searchsorted(cdf, u, side="right")
         np.minimum(idx, n - 1, out=idx)
         out[s:s + c] = idx
+
+    starts = range(0, count, block)
+    if threads > 1:
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(threads) as ex:
+            list(ex.map(one, starts))
+    else:
+        for s in starts:
+            one(s)
     return out
 
 
@@ -105,20 +119,21 @@ def chung_lu_weights(n: int, avg_deg: float, gamma: float) -> np.ndarray:
     return w
 
 
-def chung_lu(n: int, avg_deg: float, gamma: float, seed: int) -> np.ndarray:
+def chung_lu(n: int, avg_deg: float, gamma: float, seed: int, threads: int = 1) -> np.ndarray:
     """Chung-Lu power-law multigraph as a raw edge list, uint32 [M, 2].
 
     M = round(n * avg_deg / 2) pairs, each endpoint drawn independently with
     probability proportional to the capped weights.  Loops and repeated pairs
-    are left in; the listing path's graph loading removes them.
+    are left in; the listing path's graph loading removes them.  ``threads``
+    only changes how fast the draws are made, not their values.
     """
     w = chung_lu_weights(n, avg_deg, gamma)
     cdf = np.cumsum(w)
     cdf /= cdf[-1]
     m = int(round(n * avg_deg / 2.0))
     e = np.empty((m, 2), dtype=np.uint32)
-    e[:, 0] = _draw_from_cdf(cdf, seed, 0, m)
-    e[:, 1] = _draw_from_cdf(cdf, seed, 1, m)
+    e[:, 0] = _draw_from_cdf(cdf, seed, 0, m, threads=threads)
+    e[:, 1] = _draw_from_cdf(cdf, seed, 1, m, threads=threads)
     return e
 
 

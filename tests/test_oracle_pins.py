@@ -248,6 +248,41 @@ def test_duplicates_loops_and_directions_are_merged():
         assert a[1:] == b[1:]
 
 
+def test_degrees_closed_forms():
+    """Degree (Sec. 1.3) of the cleaned graph: n-1 in K_n, n-1 / 1 in a star,
+    unchanged by loops, duplicates and reversed pairs; the sum is 2m."""
+    assert oracle.Graph(9, synth.complete(9)).degrees().tolist() == [8] * 9
+    d = oracle.Graph(7, synth.star(7, hub=3)).degrees().tolist()
+    assert d == [1, 1, 1, 6, 1, 1, 1]
+    base = synth.gnp(30, 0.3, 5)
+    noisy = np.concatenate([base, base[:, ::-1], base[:20], np.array([[4, 4]], np.uint32)])
+    g = oracle.Graph(30, noisy)
+    E = _pins.simple_edge_set(base)
+    want = np.zeros(30, np.int64)
+    for a, b in E:
+        want[a] += 1
+        want[b] += 1
+    assert g.degrees().tolist() == want.tolist() and int(g.degrees().sum()) == 2 * g.m
+
+
+def test_lazy_dag_and_concurrent_listing():
+    """The DAG is built on first use; listings of disjoint seed ranges run
+    from several threads at once add up to the whole listing."""
+    from concurrent.futures import ThreadPoolExecutor
+    n = 2000
+    e = synth.chung_lu(n, 16, 2.2, 11)
+    g = oracle.Graph(n, e)
+    whole = g.list(oracle.APM, store=False)  # identity ordering, built here
+    assert g.cost(oracle.APM) == whole[3]
+    cuts = np.linspace(0, n, 9).astype(int).tolist()
+    with ThreadPoolExecutor(4) as ex:
+        parts = list(ex.map(lambda r: g.list(oracle.APM, oracle.LITERAL, r[0], r[1], store=False),
+                            zip(cuts, cuts[1:])))
+    assert sum(p[1] for p in parts) == whole[1]
+    assert sum(p[2] for p in parts) % (1 << 64) == whole[2]
+    assert sum(p[3] for p in parts) == whole[3]
+
+
 # ---- Property 1 and invariants -------------------------------------------
 
 @pytest.mark.parametrize("seed", [1, 2, 3])
