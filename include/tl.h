@@ -203,6 +203,37 @@ TL_EXPORT tl_status tl_list_triangles_range(tl_graph *g, tl_alg alg, uint32_t x_
                                   tl_consumer cb, void *user,
                                   uint64_t *n_triangles, uint64_t *n_probes);
 
+/* The work split of the listing kernels: how the outer loop of Algorithms 1
+ * and 2 (Sec. 2.1; for each vertex x, the seeds of x, each with its scanned
+ * list) is cut into device tasks.  The paper runs that loop on one thread;
+ * these are choices of the GPU path that change speed only, never the
+ * triangles, their count or the probe count.  Each "B vertex" x (w for A++,
+ * u for A+-, v for A--) with probe-set size p (the list marked in B) and W
+ * membership tests goes to one of five kernels:
+ *   small   p <= 32,   W <= warp_work: one warp, vertices grouped per task
+ *   medium  p <= 1024, W <= warp_work: one warp, vertices grouped per task
+ *   narrow  p <= 256,  W >  warp_work: one-warp CTAs, pieces of narrow_piece tests
+ *   mid     p <= 2048, W >  warp_work: 256-thread CTAs, pieces of mid_piece tests
+ *   large   p >  2048:                 1024-thread CTAs, pieces of
+ *           clamp(large_per_p * p, large_min, large_max) tests (large_max is
+ *           further capped at 1/16 of the listing's work per large CTA)
+ * Every piece rebuilds B, so larger pieces amortise that build; smaller ones
+ * balance the end of a launch. */
+typedef struct {
+  uint32_t warp_work;    /* 256 .. 4096 */
+  uint32_t narrow_piece; /* >= 1024 */
+  uint32_t mid_piece;    /* >= 1024 */
+  uint32_t large_per_p;  /* >= 1 */
+  uint32_t large_min;    /* >= 1024 */
+  uint32_t large_max;    /* >= large_min */
+} tl_tuning;
+/* The defaults (every graph starts with them). */
+TL_EXPORT tl_status tl_default_tuning(tl_tuning *out);
+/* Set the work split of later listings on g (NULL restores the defaults).
+ * A value outside the ranges above -> TL_EINVAL, and g keeps its split. */
+TL_EXPORT tl_status tl_set_tuning(tl_graph *g, const tl_tuning *t);
+TL_EXPORT tl_status tl_get_tuning(const tl_graph *g, tl_tuning *out);
+
 /* A ready-made consumer: count the triples and add up their set hash
  *   H = sum over triples of h(a,b,c)  (mod 2^64),
  *   h(a,b,c) = mix(mix(mix(a + G) + b + G) + c + G),
@@ -355,17 +386,19 @@ TL_EXPORT tl_status tl_graph_csr(const tl_graph *g, int dir, uint64_t *off, uint
 
 /* Counters of the last tl_list_triangles* call on this graph, for benches
  * and profiling.  kernel_ms are CUDA-event durations of the listing kernels
- * (index 0: small-, 1: medium-, 2: mid-, 3: large-vertex kernel), recorded on the
- * handle's stream around each launch. */
+ * (index 0: small-, 1: medium-, 2: narrow-, 3: mid-, 4: large-vertex
+ * kernel; see tl_tuning), recorded on the handle's stream around each
+ * launch. */
+#define TL_KERNELS 5
 typedef struct {
   uint64_t launches;     /* listing kernel launches */
   uint64_t chunks;       /* chunks handed to the consumer */
   uint64_t triangles;    /* triangles listed */
   uint64_t probes;       /* membership tests performed */
-  uint64_t tasks[4];     /* tasks of each kernel: 0 small, 1 medium, 2 mid, 3 large */
-  double kernel_ms[4];   /* summed device time of each kernel */
-  uint64_t kernel_probes[4];     /* membership tests done by each kernel */
-  uint64_t kernel_triangles[4];  /* triangles found by each kernel */
+  uint64_t tasks[TL_KERNELS];     /* tasks of each kernel */
+  double kernel_ms[TL_KERNELS];   /* summed device time of each kernel */
+  uint64_t kernel_probes[TL_KERNELS];     /* membership tests done by each kernel */
+  uint64_t kernel_triangles[TL_KERNELS];  /* triangles found by each kernel */
   double bucketize_ms;           /* host wall time of the work split (a6) */
   double consumer_ms;            /* host wall time inside the consumer */
   double wall_ms;                /* host wall time of the whole call */

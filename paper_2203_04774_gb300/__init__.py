@@ -56,12 +56,24 @@ class RequestResult(ctypes.Structure):
                 ("t_submit_ns", _U64), ("t_admit_ns", _U64), ("t_done_ns", _U64)]
 
 
+TL_KERNELS = 5  # small, medium, narrow, mid, large
+
+
 class ListStats(ctypes.Structure):
     _fields_ = [("launches", _U64), ("chunks", _U64), ("triangles", _U64), ("probes", _U64),
-                ("tasks", _U64 * 4), ("kernel_ms", ctypes.c_double * 4),
-                ("kernel_probes", _U64 * 4), ("kernel_triangles", _U64 * 4),
+                ("tasks", _U64 * TL_KERNELS), ("kernel_ms", ctypes.c_double * TL_KERNELS),
+                ("kernel_probes", _U64 * TL_KERNELS), ("kernel_triangles", _U64 * TL_KERNELS),
                 ("bucketize_ms", ctypes.c_double), ("consumer_ms", ctypes.c_double),
                 ("wall_ms", ctypes.c_double)]
+
+
+class Tuning(ctypes.Structure):
+    """tl_tuning: the work split of the listing kernels (speed only)."""
+    _fields_ = [("warp_work", _U32), ("narrow_piece", _U32), ("mid_piece", _U32),
+                ("large_per_p", _U32), ("large_min", _U32), ("large_max", _U32)]
+
+    def as_dict(self) -> dict:
+        return {name: int(getattr(self, name)) for name, _ in self._fields_}
 
 
 SIGNATURES = {
@@ -78,6 +90,9 @@ SIGNATURES = {
     "tl_count_hash": ([_P, _U64, _U64, _P], _I),
     "tl_count_hash_release": ([ctypes.POINTER(CountHashState)], None),
     "tl_graph_csr": ([_P, _I, _P, _P], _I),
+    "tl_default_tuning": ([ctypes.POINTER(Tuning)], _I),
+    "tl_set_tuning": ([_P, ctypes.POINTER(Tuning)], _I),
+    "tl_get_tuning": ([_P, ctypes.POINTER(Tuning)], _I),
     "tl_server_create": ([ctypes.POINTER(_P), ctypes.POINTER(ServerConfig)], _I),
     "tl_server_add_graph": ([_P, _P, ctypes.POINTER(_U32)], _I),
     "tl_server_add_ordering": ([_P, _U32, _P, _I, ctypes.POINTER(_U32)], _I),
@@ -289,6 +304,31 @@ def tl_last_list_stats(g) -> dict:
             "kernel_triangles": [int(v) for v in st.kernel_triangles],
             "bucketize_ms": float(st.bucketize_ms), "consumer_ms": float(st.consumer_ms),
             "wall_ms": float(st.wall_ms)}
+
+
+def tl_default_tuning() -> dict:
+    t = Tuning()
+    _check(lib().tl_default_tuning(ctypes.byref(t)), "tl_default_tuning")
+    return t.as_dict()
+
+
+def tl_set_tuning(g, tuning: dict | None) -> None:
+    """Set the work split of later listings on g (None: the defaults).  Keys
+    missing from `tuning` keep the graph's current values."""
+    if tuning is None:
+        _check(lib().tl_set_tuning(g, None), "tl_set_tuning")
+        return
+    t = Tuning()
+    _check(lib().tl_get_tuning(g, ctypes.byref(t)), "tl_get_tuning")
+    for k, v in tuning.items():
+        setattr(t, k, int(v))
+    _check(lib().tl_set_tuning(g, ctypes.byref(t)), "tl_set_tuning")
+
+
+def tl_get_tuning(g) -> dict:
+    t = Tuning()
+    _check(lib().tl_get_tuning(g, ctypes.byref(t)), "tl_get_tuning")
+    return t.as_dict()
 
 
 def tl_kernel_launches() -> int:

@@ -61,6 +61,19 @@ struct PinnedCtl {
 }  // namespace
 }  // namespace tl
 
+namespace {
+tl_tuning tl_default_tuning_value() {
+  tl_tuning t;
+  t.warp_work = (uint32_t)tl::kWarpWorkMax;
+  t.narrow_piece = 1u << 14;
+  t.mid_piece = 1u << 16;
+  t.large_per_p = 64;
+  t.large_min = 1u << 16;
+  t.large_max = 1u << 22;
+  return t;
+}
+}  // namespace
+
 struct tl_graph {
   tl::DeviceGraph g;
   // listing workspace
@@ -68,23 +81,27 @@ struct tl_graph {
   uint64_t rretry_cap = 0;  // RetryPiece records per half of rretry
   // per-vertex classification (tiers 0, 1: weights and flags; tiers 2, 3: pieces),
   // their prefixes, and the compacted vertex lists of tiers 0 and 1
-  tl::DevBuf tw[2], tf[2], tpref[2], tpos[2], tx[2], twp[2], tstart[2], pieces[2],
-      piece_prefix[2], task_x[2];
+  tl::DevBuf tw[2], tf[2], tpref[2], tpos[2], tx[2], twp[2], tstart[2], pieces[3],
+      piece_prefix[3], task_x[3];
   tl::PinnedCtl *pctl = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr};
   tl_list_stats stats{};
   int cached_alg = -1;
   uint32_t cached_xb = 0, cached_xe = 0;
-  uint64_t n_tasks[tl::kTiers] = {0, 0, 0, 0};
+  uint64_t n_tasks[tl::kTiers] = {0, 0, 0, 0, 0};
+  // the work split: as set by tl_set_tuning, and as used by the cached tables
+  tl_tuning tuning = tl_default_tuning_value();
+  tl::Tuning used_tu{};
   uint64_t tier_count[2] = {0, 0};
   void bind(cudaStream_t s) {
     g.bind(s);
     for (tl::DevBuf *b : {&wseed, &WP, &ctl, &chunks, &slabs, &retry, &rretry, &ghash})
       b->stream = s;
     for (int t = 0; t < 2; ++t)
-      for (tl::DevBuf *b : {&tw[t], &tf[t], &tpref[t], &tpos[t], &tx[t], &twp[t], &tstart[t],
-                            &pieces[t], &piece_prefix[t], &task_x[t]})
+      for (tl::DevBuf *b : {&tw[t], &tf[t], &tpref[t], &tpos[t], &tx[t], &twp[t], &tstart[t]})
         b->stream = s;
+    for (int t = 0; t < 3; ++t)
+      for (tl::DevBuf *b : {&pieces[t], &piece_prefix[t], &task_x[t]}) b->stream = s;
   }
   ~tl_graph() {
     delete pctl;
@@ -147,17 +164,56 @@ Sides sides(const tl::DeviceGraph &g, int alg) {
   return Sides{io, oo, io, ia, oa, ia};
 }
 
-// a6: per-seed-edge work prefix and the task counts of both kernels.
+template <class T>
+T read_dev(const T *p, cudaStream_t s) {
+  T v;
+  TL_CUDA(cudaMemcpyAsync(&v, p, sizeof(T), cudaMemcpyDeviceToHost, s));
+  TL_CUDA(cudaStreamSynchronize(s));
+  return v;
+}
+
+// The work split used for one listing: the caller's tuning, with large pieces
+// capped at 1/16 of an even share of the range's work per large-vertex CTA,
+// so that no single piece holds up the end of the launch on a small graph.
+tl::Tuning effective_tuning(const tl_tuning &t, uint64_t range_work) {
+  tl::Tuning tu;
+  tu.warp_work = t.warp_work;
+  tu.narrow_piece = t.narrow_piece;
+  tu.mid_piece = t.mid_piece;
+  tu.large_per_p = t.large_per_p;
+  tu.large_min = t.large_min;
+  const uint64_t cap = range_work / (16ull * (uint64_t)tl::tier_grid(tl::kTierLarge));
+  uint64_t mx = std::min<uint64_t>(t.large_max, std::max<uint64_t>(cap, t.large_min));
+  tu.large_max = (uint32_t)mx;
+  return tu;
+}
+
+bool same_tuning(const tl::Tuning &a, const tl::Tuning &b) {
+  return a.warp_work == b.warp_work && a.narrow_piece == b.narrow_piece &&
+         a.mid_piece == b.mid_piece && a.large_per_p == b.large_per_p &&
+         a.large_min == b.large_min && a.large_max == b.large_max;
+}
+
+// a6: per-seed-edge work prefix and the task counts of every kernel.
 void bucketize(tl_graph *G, int alg, uint32_t xb, uint32_t xe) {
-  if (G->cached_alg == alg && G->cached_xb == xb && G->cached_xe == xe) return;
   tl::DeviceGraph &g = G->g;
   cudaStream_t s = g.stream;
   const uint64_t m = g.m;
   const Sides sd = sides(g, alg);
-  G->wseed.reserve((m ? m : 1) * 4);
-  G->WP.reserve((m + 1) * 8);
-  if (m) tl::launch_seed_work(sd.sadj, m, sd.scan_off, G->wseed.as<uint32_t>(), s);
-  tl::exclusive_scan_u32_to_u64(G->wseed.as<uint32_t>(), G->WP.as<uint64_t>(), m, g.scan_tmp, s);
+  if (!(G->cached_alg == alg && G->cached_xb == xb && G->cached_xe == xe)) {
+    G->wseed.reserve((m ? m : 1) * 4);
+    G->WP.reserve((m + 1) * 8);
+    if (m) tl::launch_seed_work(sd.sadj, m, sd.scan_off, G->wseed.as<uint32_t>(), s);
+    tl::exclusive_scan_u32_to_u64(G->wseed.as<uint32_t>(), G->WP.as<uint64_t>(), m, g.scan_tmp,
+                                  s);
+  }
+  const uint64_t kb = read_dev(sd.soff + xb, s), ke = read_dev(sd.soff + xe, s);
+  const uint64_t range_work =
+      read_dev(G->WP.as<uint64_t>() + ke, s) - read_dev(G->WP.as<uint64_t>() + kb, s);
+  const tl::Tuning tu = effective_tuning(G->tuning, range_work);
+  if (G->cached_alg == alg && G->cached_xb == xb && G->cached_xe == xe &&
+      same_tuning(tu, G->used_tu))
+    return;
   const uint64_t nr = xe - xb;
   const uint64_t nr1 = nr ? nr : 1;
   for (int t = 0; t < 2; ++t) {
@@ -168,14 +224,16 @@ void bucketize(tl_graph *G, int alg, uint32_t xb, uint32_t xe) {
     G->tx[t].reserve(nr1 * 4);
     G->twp[t].reserve((nr + 1) * 8);
   }
-  for (int t = 0; t < 2; ++t) {
+  for (int t = 0; t < 3; ++t) {
     G->pieces[t].reserve(nr1 * 8);
     G->piece_prefix[t].reserve((nr + 1) * 8);
   }
   if (nr)
-    tl::launch_classify(sd.poff, sd.soff, G->WP.as<uint64_t>(), xb, xe, G->tw[0].as<uint64_t>(),
-                        G->tw[1].as<uint64_t>(), G->tf[0].as<uint32_t>(), G->tf[1].as<uint32_t>(),
-                        G->pieces[0].as<uint64_t>(), G->pieces[1].as<uint64_t>(), s);
+    tl::launch_classify(sd.poff, sd.soff, G->WP.as<uint64_t>(), xb, xe, tu,
+                        G->tw[0].as<uint64_t>(), G->tw[1].as<uint64_t>(),
+                        G->tf[0].as<uint32_t>(), G->tf[1].as<uint32_t>(),
+                        G->pieces[0].as<uint64_t>(), G->pieces[1].as<uint64_t>(),
+                        G->pieces[2].as<uint64_t>(), s);
   for (int t = 0; t < 2; ++t) {
     tl::exclusive_scan_u64(G->tw[t].as<uint64_t>(), G->tpref[t].as<uint64_t>(), nr, g.scan_tmp, s);
     tl::exclusive_scan_u32_to_u64(G->tf[t].as<uint32_t>(), G->tpos[t].as<uint64_t>(), nr,
@@ -184,30 +242,30 @@ void bucketize(tl_graph *G, int alg, uint32_t xb, uint32_t xe) {
                             G->tpref[t].as<uint64_t>(), xb, nr, G->tx[t].as<uint32_t>(),
                             G->twp[t].as<uint64_t>(), s);
   }
-  for (int t = 0; t < 2; ++t)
+  for (int t = 0; t < 3; ++t)
     tl::exclusive_scan_u64(G->pieces[t].as<uint64_t>(), G->piece_prefix[t].as<uint64_t>(), nr,
                            g.scan_tmp, s);
-  // totals: weights of tiers 0 and 1, their vertex counts, pieces of tiers 2 and 3
-  uint64_t tot[6];
+  // totals: weights of tiers 0 and 1, their vertex counts, pieces of tiers 2, 3 and 4
+  uint64_t tot[7];
   TL_CUDA(cudaMemcpyAsync(&tot[0], G->tpref[0].as<uint64_t>() + nr, 8, cudaMemcpyDeviceToHost, s));
   TL_CUDA(cudaMemcpyAsync(&tot[1], G->tpref[1].as<uint64_t>() + nr, 8, cudaMemcpyDeviceToHost, s));
   TL_CUDA(cudaMemcpyAsync(&tot[2], G->tpos[0].as<uint64_t>() + nr, 8, cudaMemcpyDeviceToHost, s));
   TL_CUDA(cudaMemcpyAsync(&tot[3], G->tpos[1].as<uint64_t>() + nr, 8, cudaMemcpyDeviceToHost, s));
-  TL_CUDA(cudaMemcpyAsync(&tot[4], G->piece_prefix[0].as<uint64_t>() + nr, 8,
-                          cudaMemcpyDeviceToHost, s));
-  TL_CUDA(cudaMemcpyAsync(&tot[5], G->piece_prefix[1].as<uint64_t>() + nr, 8,
-                          cudaMemcpyDeviceToHost, s));
+  for (int t = 0; t < 3; ++t)
+    TL_CUDA(cudaMemcpyAsync(&tot[4 + t], G->piece_prefix[t].as<uint64_t>() + nr, 8,
+                            cudaMemcpyDeviceToHost, s));
   TL_CUDA(cudaStreamSynchronize(s));
-  G->n_tasks[0] = (tot[0] + tl::kWarpWork - 1) / tl::kWarpWork;
-  G->n_tasks[1] = (tot[1] + tl::kWarpWork - 1) / tl::kWarpWork;
-  G->n_tasks[2] = tot[4];
-  G->n_tasks[3] = tot[5];
+  G->n_tasks[0] = (tot[0] + tu.warp_work - 1) / tu.warp_work;
+  G->n_tasks[1] = (tot[1] + tu.warp_work - 1) / tu.warp_work;
+  for (int t = 0; t < 3; ++t) G->n_tasks[2 + t] = tot[4 + t];
   G->tier_count[0] = tot[2];
   G->tier_count[1] = tot[3];
   for (int t = 0; t < 2; ++t) {
     G->tstart[t].reserve((G->n_tasks[t] + 1) * 4);
     tl::launch_task_bounds(G->twp[t].as<uint64_t>(), G->tier_count[t], G->n_tasks[t],
-                           G->tstart[t].as<uint32_t>(), s);
+                           tu.warp_work, G->tstart[t].as<uint32_t>(), s);
+  }
+  for (int t = 0; t < 3; ++t) {
     G->task_x[t].reserve((G->n_tasks[2 + t] ? G->n_tasks[2 + t] : 1) * 4);
     tl::launch_task_owner(G->piece_prefix[t].as<uint64_t>(), xb, nr, G->task_x[t].as<uint32_t>(),
                           s);
@@ -215,6 +273,7 @@ void bucketize(tl_graph *G, int alg, uint32_t xb, uint32_t xe) {
   G->cached_alg = alg;
   G->cached_xb = xb;
   G->cached_xe = xe;
+  G->used_tu = tu;
 }
 
 struct Phase {
@@ -255,8 +314,9 @@ tl_status list_impl(tl_graph *G, int alg, uint32_t xb, uint32_t xe, size_t chunk
   G->slabs.reserve(slab_words * 12);
   // hub tables in global memory, needed only when the bitmap over all ranks
   // does not fit in shared memory
-  const bool need_ghash = g.n > tl::kBitmapMaxN && G->n_tasks[3] > 0;
-  if (need_ghash) G->ghash.reserve((uint64_t)tl::tier_grid(3) * tl::kGHashSlots * 4);
+  const bool need_ghash = g.n > tl::kBitmapMaxN && G->n_tasks[tl::kTierLarge] > 0;
+  if (need_ghash)
+    G->ghash.reserve((uint64_t)tl::tier_grid(tl::kTierLarge) * tl::kGHashSlots * 4);
   G->retry.reserve(2 * max_tasks * 4);
   G->ctl.reserve(sizeof(tl::ListCtl));
   if (!G->pctl) G->pctl = new tl::PinnedCtl();
@@ -266,7 +326,10 @@ tl_status list_impl(tl_graph *G, int alg, uint32_t xb, uint32_t xe, size_t chunk
   // CTA tiers: a launch queues at most one record per CTA and piece, and a
   // CTA runs at most two pieces after the chunk fills (the current one and
   // the one it had already fetched); plus the records it did not fetch
-  const uint64_t warps_cta = 2 * std::max<uint64_t>(tl::tier_grid(2), tl::tier_grid(3));
+  const uint64_t warps_cta =
+      2 * std::max<uint64_t>({(uint64_t)tl::tier_grid(tl::kTierNarrow),
+                              (uint64_t)tl::tier_grid(tl::kTierMid),
+                              (uint64_t)tl::tier_grid(tl::kTierLarge)});
   auto rr_half = [&](int h) { return G->rretry.as<tl::RetryPiece>() + h * G->rretry_cap; };
   auto reserve_ranges = [&](int in_half, uint64_t n_in, uint64_t need) {
     if (need <= G->rretry_cap) return;
@@ -298,6 +361,7 @@ tl_status list_impl(tl_graph *G, int alg, uint32_t xb, uint32_t xe, size_t chunk
   a.chunk_cap = cap;
   a.slabs = G->slabs.as<uint32_t>();
   a.ghash = need_ghash ? G->ghash.as<uint32_t>() : nullptr;
+  a.tu = G->used_tu;
 
   if (!G->ev[0]) {
     TL_CUDA(cudaEventCreate(&G->ev[0]));
@@ -307,8 +371,11 @@ tl_status list_impl(tl_graph *G, int alg, uint32_t xb, uint32_t xe, size_t chunk
   for (int t = 0; t < tl::kTiers; ++t) st.tasks[t] = G->n_tasks[t];
   G->stats = st;
   constexpr int kPhases = tl::kTiers;
-  Phase phases[kPhases] = {
-      {0, G->n_tasks[0]}, {1, G->n_tasks[1]}, {2, G->n_tasks[2]}, {3, G->n_tasks[3]}};
+  Phase phases[kPhases] = {{0, G->n_tasks[0]},
+                           {1, G->n_tasks[1]},
+                           {2, G->n_tasks[2]},
+                           {3, G->n_tasks[3]},
+                           {4, G->n_tasks[4]}};
   int cur = 0, rsel = 0;
   uint64_t filled = 0, chunk_idx = 0, total_tri = 0, total_probes = 0;
   int pending = -1;
@@ -602,6 +669,34 @@ void tl_count_hash_release(tl_count_hash_state *s) {
     cudaFree(s->scratch);
     s->scratch = nullptr;
   }
+}
+
+tl_status tl_default_tuning(tl_tuning *out) {
+  TL_API_BEGIN
+  if (!out) tl::fail(TL_EINVAL, "out is NULL");
+  *out = tl_default_tuning_value();
+  TL_API_END
+}
+
+tl_status tl_set_tuning(tl_graph *G, const tl_tuning *t) {
+  TL_API_BEGIN
+  if (!G) tl::fail(TL_EINVAL, "graph is NULL");
+  const tl_tuning v = t ? *t : tl_default_tuning_value();
+  if (v.warp_work < 256 || v.warp_work > tl::kWarpWorkMax)
+    tl::fail(TL_EINVAL, "warp_work must be in [256, 4096]");
+  if (v.narrow_piece < 1024 || v.mid_piece < 1024 || v.large_min < 1024)
+    tl::fail(TL_EINVAL, "narrow_piece, mid_piece and large_min must be >= 1024");
+  if (v.large_per_p < 1 || v.large_max < v.large_min)
+    tl::fail(TL_EINVAL, "large_per_p must be >= 1 and large_max >= large_min");
+  G->tuning = v;
+  TL_API_END
+}
+
+tl_status tl_get_tuning(const tl_graph *G, tl_tuning *out) {
+  TL_API_BEGIN
+  if (!G || !out) tl::fail(TL_EINVAL, "NULL argument");
+  *out = G->tuning;
+  TL_API_END
 }
 
 tl_status tl_graph_csr(const tl_graph *G, int dir, uint64_t *off, uint32_t *adj) {

@@ -22,7 +22,7 @@
 //
 // B (the boolean array of the algorithms) per tier:
 //   small/medium x: a per-warp hash table in shared memory (load <= 1/2), one
-//   warp per x, vertices grouped into tasks of about kWarpWork tests;
+//   warp per x, vertices grouped into tasks of about warp_work tests;
 //   mid/large x: one structure per CTA -- a bucketed hash, a bitmap over all
 //   ranks when n is small enough (literally B, bit-packed), a shared filter in
 //   front of a global hash for hubs of large graphs, or binary search in the
@@ -311,12 +311,16 @@ __device__ __forceinline__ bool fetch_piece(const ListArgs &a, uint32_t &x, uint
     x = retry->x;
     return true;
   }
-  const uint64_t t = a.fresh_base + (idx - a.n_retry);
-  if (t >= a.n_tasks) return false;
+  const uint64_t f = a.fresh_base + (idx - a.n_retry);
+  if (f >= a.n_tasks) return false;
+  // fresh tasks from the last down: under a degree ordering the largest
+  // vertices have the highest ranks, and starting with them keeps the end of
+  // the launch from waiting on one big piece
+  const uint64_t t = a.n_tasks - 1 - f;
   x = a.task_x[t];
   const uint64_t piece = t - a.piece_prefix[x - a.x_begin];
   const uint64_t w1 = a.WP[a.soff[x + 1]];
-  const uint64_t pw = piece_work(a.tier, a.poff[x + 1] - a.poff[x]);
+  const uint64_t pw = piece_work(a.tu, a.tier, a.poff[x + 1] - a.poff[x]);
   ia = a.WP[a.soff[x]] + piece * pw;
   ib = ia + pw < w1 ? ia + pw : w1;
   return true;
@@ -553,18 +557,22 @@ __global__ void __launch_bounds__(kWarpThreads, 4) k_list_warp(ListArgs a) {
   }
 }
 
-// ---- mid and large vertices: one CTA per piece, B shared by the CTA -------
-//   TIER 2 (mid, p <= 2048): open-addressing hash of <= 8192 slots.
-//   TIER 3 (large): a bitmap over all ranks when n <= kBitmapMaxN (mode 0),
-//   else a hash of <= kHashMaxSlots slots (mode 1), else a filter in shared
-//   memory + the CTA's hash table in global memory (mode 3), else binary
-//   search in the sorted row (mode 2).
+// ---- narrow, mid and large vertices: one CTA per piece, B shared by the CTA
+//   narrow (p <= 256, one warp per CTA) and mid (p <= 2048): bucketed hash of
+//   <= 1024 resp. 8192 slots (load <= 1/4).
+//   large: a bitmap over all ranks when n <= kBitmapMaxN (mode 0), else a
+//   hash of <= kHashMaxSlots slots (mode 1), else a filter in shared memory +
+//   the CTA's hash table in global memory (mode 3), else binary search in the
+//   sorted row (mode 2).
 
 template <int THREADS, int TIER>
-__global__ void __launch_bounds__(THREADS, TIER == 3 ? 1 : 4) k_list_cta(ListArgs a) {
+__global__ void __launch_bounds__(THREADS, TIER == kTierLarge ? 1 : (TIER == kTierMid ? 4 : 32))
+    k_list_cta(ListArgs a) {
   // probe structure (bitmap, hash or filter) | one output buffer per warp
   extern __shared__ __align__(16) uint32_t sm[];
-  constexpr uint32_t kProbeWords = (TIER == 2 ? kMidProbeBytes : kLargeProbeBytes) / 4;
+  constexpr uint32_t kProbeWords =
+      (TIER == kTierNarrow ? kNarrowProbeBytes
+                           : (TIER == kTierMid ? kMidProbeBytes : kLargeProbeBytes)) / 4;
   // the next piece of work (one test range per warp), fetched by the first
   // warp done with the current one while the others finish (or by thread 0
   // before the first); the ranges of warps stopped by a full chunk
@@ -574,7 +582,7 @@ __global__ void __launch_bounds__(THREADS, TIER == 3 ? 1 : 4) k_list_cta(ListArg
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   WarpOut o{sm + kProbeWords + (uint32_t)wid * 2 * kWarpBuf, 0, 0, 0, false};
   uint32_t unused = 0;
-  const bool use_bitmap = TIER == 3 && a.n <= kBitmapMaxN;
+  const bool use_bitmap = TIER == kTierLarge && a.n <= kBitmapMaxN;
   if (use_bitmap) {
     const uint32_t words = (a.n + 31) >> 5;
     for (uint32_t i = threadIdx.x; i < words; i += THREADS) sm[i] = 0;
@@ -607,14 +615,15 @@ __global__ void __launch_bounds__(THREADS, TIER == 3 ? 1 : 4) k_list_cta(ListArg
       s_mode = 0;
       return;
     }
-    // mid tier: load <= 1/4, so most lookups end at the first bucket
-    const uint32_t max_slots = TIER == 2 ? (uint32_t)kMidSlots : kHashMaxSlots;
-    const uint64_t want = TIER == 2 ? 4 * p : 2 * p;
+    // narrow and mid tiers: load <= 1/4, so most lookups end at the first bucket
+    const uint32_t max_slots = TIER == kTierNarrow ? (uint32_t)kNarrowSlots
+                               : (TIER == kTierMid ? (uint32_t)kMidSlots : kHashMaxSlots);
+    const uint64_t want = TIER == kTierLarge ? 2 * p : 4 * p;
     uint32_t lg = 6;
     while ((1ull << lg) < want && (1u << lg) < max_slots) ++lg;
     s_lg = lg;
     s_mode = (2 * p <= (1ull << lg)) ? 1 : 2;  // 2: too large, binary search
-    if (TIER == 3 && s_mode == 2 && a.ghash && 2 * p <= kGHashSlots) {
+    if (TIER == kTierLarge && s_mode == 2 && a.ghash && 2 * p <= kGHashSlots) {
       // 3: shared-memory filter + this CTA's hash table in global memory
       lg = 6;
       while ((1ull << lg) < 2 * p) ++lg;
@@ -746,28 +755,30 @@ __global__ void k_seed_work(const uint32_t *__restrict__ sadj, uint64_t m,
 
 __global__ void k_classify(const uint64_t *__restrict__ poff, const uint64_t *__restrict__ soff,
                            const uint64_t *__restrict__ WP,
-                           uint32_t x_begin, uint32_t x_end, uint64_t *__restrict__ w0,
+                           uint32_t x_begin, uint32_t x_end, Tuning tu, uint64_t *__restrict__ w0,
                            uint64_t *__restrict__ w1, uint32_t *__restrict__ f0,
                            uint32_t *__restrict__ f1, uint64_t *__restrict__ pieces2,
-                           uint64_t *__restrict__ pieces3) {
+                           uint64_t *__restrict__ pieces3, uint64_t *__restrict__ pieces4) {
   const uint64_t nr = x_end - x_begin;
   for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < nr;
        r += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t x = x_begin + (uint32_t)r;
     const uint64_t W = WP[soff[x + 1]] - WP[soff[x]];
     const uint64_t p = poff[x + 1] - poff[x];
-    uint64_t a0 = 0, a1 = 0, n2 = 0, n3 = 0;
+    uint64_t a0 = 0, a1 = 0, n2 = 0, n3 = 0, n4 = 0;
     // every prescribed test runs, also when P_x is empty (possible for A--,
     // whose seeds are not its probe set): the work then equals the cost
     if (W > 0) {
-      if (p <= kSmallMaxP && W <= kWarpWork)
+      if (p <= kSmallMaxP && W <= tu.warp_work) {
         a0 = W + kVertexCost;
-      else if (p <= kMediumMaxP && W <= kWarpWork)
+      } else if (p <= kMediumMaxP && W <= tu.warp_work) {
         a1 = W + kVertexCost;
-      else if (p <= kMidMaxP)
-        n2 = (W + piece_work(2, p) - 1) / piece_work(2, p);
-      else
-        n3 = (W + piece_work(3, p) - 1) / piece_work(3, p);
+      } else {
+        const int tier = p <= kNarrowMaxP ? kTierNarrow : (p <= kMidMaxP ? kTierMid : kTierLarge);
+        const uint64_t pw = piece_work(tu, tier, p);
+        const uint64_t np = (W + pw - 1) / pw;
+        if (tier == kTierNarrow) n2 = np; else if (tier == kTierMid) n3 = np; else n4 = np;
+      }
     }
     w0[r] = a0;
     w1[r] = a1;
@@ -775,6 +786,7 @@ __global__ void k_classify(const uint64_t *__restrict__ poff, const uint64_t *__
     f1[r] = a1 ? 1u : 0u;
     pieces2[r] = n2;
     pieces3[r] = n3;
+    pieces4[r] = n4;
   }
 }
 
@@ -793,10 +805,10 @@ __global__ void k_compact_tier(const uint32_t *__restrict__ flags, const uint64_
 }
 
 __global__ void k_task_bounds(const uint64_t *__restrict__ wp, uint64_t count, uint64_t n_tasks,
-                              uint32_t *__restrict__ task_start) {
+                              uint64_t warp_work, uint32_t *__restrict__ task_start) {
   for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t <= n_tasks;
        t += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t i = lower_bound_u64(wp, count + 1, t * kWarpWork);
+    const uint64_t i = lower_bound_u64(wp, count + 1, t * warp_work);
     task_start[t] = (uint32_t)(i < count ? i : count);
   }
 }
@@ -833,11 +845,11 @@ void launch_seed_work(const uint32_t *sadj, uint64_t m, const uint64_t *scan_off
 }
 
 void launch_classify(const uint64_t *poff, const uint64_t *soff, const uint64_t *WP,
-                     uint32_t x_begin, uint32_t x_end,
+                     uint32_t x_begin, uint32_t x_end, const Tuning &tu,
                      uint64_t *w0, uint64_t *w1, uint32_t *f0, uint32_t *f1, uint64_t *pieces2,
-                     uint64_t *pieces3, cudaStream_t s) {
+                     uint64_t *pieces3, uint64_t *pieces4, cudaStream_t s) {
   k_classify<<<grid_for((uint64_t)(x_end - x_begin), 256), 256, 0, s>>>(
-      poff, soff, WP, x_begin, x_end, w0, w1, f0, f1, pieces2, pieces3);
+      poff, soff, WP, x_begin, x_end, tu, w0, w1, f0, f1, pieces2, pieces3, pieces4);
   TL_CHECK_LAUNCH();
 }
 
@@ -850,8 +862,9 @@ void launch_compact_tier(const uint32_t *flags, const uint64_t *pos, const uint6
 }
 
 void launch_task_bounds(const uint64_t *wp_list, uint64_t count, uint64_t n_tasks,
-                        uint32_t *task_start, cudaStream_t s) {
-  k_task_bounds<<<grid_for(n_tasks + 1, 256), 256, 0, s>>>(wp_list, count, n_tasks, task_start);
+                        uint64_t warp_work, uint32_t *task_start, cudaStream_t s) {
+  k_task_bounds<<<grid_for(n_tasks + 1, 256), 256, 0, s>>>(wp_list, count, n_tasks, warp_work,
+                                                           task_start);
   TL_CHECK_LAUNCH();
 }
 
@@ -871,8 +884,11 @@ int tier_grid(int tier) {
     Grids r;
     r.g[0] = occupancy_grid(k_list_warp<kSmallSlots>, kWarpThreads, kSmemSmall);
     r.g[1] = occupancy_grid(k_list_warp<kMediumSlots>, kWarpThreads, kSmemMedium);
-    r.g[2] = occupancy_grid(k_list_cta<kMidThreads, 2>, kMidThreads, kSmemMid);
-    r.g[3] = occupancy_grid(k_list_cta<kLargeThreads, 3>, kLargeThreads, kLargeSmemBytes);
+    r.g[2] = occupancy_grid(k_list_cta<kNarrowThreads, kTierNarrow>, kNarrowThreads,
+                            kNarrowSmemBytes);
+    r.g[3] = occupancy_grid(k_list_cta<kMidThreads, kTierMid>, kMidThreads, kSmemMid);
+    r.g[4] = occupancy_grid(k_list_cta<kLargeThreads, kTierLarge>, kLargeThreads,
+                            kLargeSmemBytes);
     return r;
   }();
   return grids.g[tier];
@@ -885,7 +901,7 @@ uint64_t list_fixed_bytes(uint64_t chunk_bytes) {
     slab = w > slab ? w : slab;
   }
   return 2 * (chunk_bytes / 12) * 12 + slab * 12 +
-         (uint64_t)tier_grid(3) * kGHashSlots * 4;
+         (uint64_t)tier_grid(kTierLarge) * kGHashSlots * 4;
 }
 
 void launch_list(int tier, const ListArgs &a, cudaStream_t s) {
@@ -894,10 +910,12 @@ void launch_list(int tier, const ListArgs &a, cudaStream_t s) {
     k_list_warp<kSmallSlots><<<grid, kWarpThreads, kSmemSmall, s>>>(a);
   } else if (tier == 1) {
     k_list_warp<kMediumSlots><<<grid, kWarpThreads, kSmemMedium, s>>>(a);
-  } else if (tier == 2) {
-    k_list_cta<kMidThreads, 2><<<grid, kMidThreads, kSmemMid, s>>>(a);
+  } else if (tier == kTierNarrow) {
+    k_list_cta<kNarrowThreads, kTierNarrow><<<grid, kNarrowThreads, kNarrowSmemBytes, s>>>(a);
+  } else if (tier == kTierMid) {
+    k_list_cta<kMidThreads, kTierMid><<<grid, kMidThreads, kSmemMid, s>>>(a);
   } else {
-    k_list_cta<kLargeThreads, 3><<<grid, kLargeThreads, kLargeSmemBytes, s>>>(a);
+    k_list_cta<kLargeThreads, kTierLarge><<<grid, kLargeThreads, kLargeSmemBytes, s>>>(a);
   }
   TL_CHECK_LAUNCH();
 }

@@ -5,34 +5,47 @@
 
 namespace tl {
 
-// Tiers of B vertices x (by probe-set size p = |P_x| and work W_x):
-//   0 small:  p <= 32,   W <= kWarpWork  -- one warp per x, 64-slot hash per warp
-//   1 medium: p <= 1024, W <= kWarpWork  -- one warp per x, 2048-slot hash per warp
-//   2 mid:    p <= 2048, W >  kWarpWork  -- 256-thread CTA per piece, 8192-slot bucketed hash
-//   3 large:  p >  2048                  -- 1024-thread CTA per piece, bitmap / hash
-constexpr int kTiers = 4;
+// Tiers of B vertices x (by probe-set size p = |P_x| and work W_x, the
+// number of membership tests of x; ww = Tuning::warp_work):
+//   0 small:  p <= 32,   W <= ww  -- one warp per x, 64-slot hash per warp
+//   1 medium: p <= 1024, W <= ww  -- one warp per x, 2048-slot hash per warp
+//   2 narrow: p <= 256,  W >  ww  -- one-warp CTA per piece, 1024-slot bucketed hash
+//   3 mid:    p <= 2048, W >  ww  -- 256-thread CTA per piece, 8192-slot bucketed hash
+//   4 large:  p >  2048           -- 1024-thread CTA per piece, bitmap / hash
+constexpr int kTiers = 5;
+constexpr int kTierSmall = 0, kTierMedium = 1, kTierNarrow = 2, kTierMid = 3, kTierLarge = 4;
 constexpr int kWarpThreads = 256;
+constexpr int kNarrowThreads = 32;
 constexpr int kMidThreads = 256;
 constexpr int kLargeThreads = 1024;
-constexpr uint32_t kSmallMaxP = 32, kMediumMaxP = 1024, kMidMaxP = 2048;
+constexpr uint32_t kSmallMaxP = 32, kMediumMaxP = 1024, kNarrowMaxP = 256, kMidMaxP = 2048;
 constexpr int kSmallSlots = 64, kMediumSlots = 2048;  // per warp, >= 2p (load <= 1/2)
+constexpr int kNarrowSlots = 1024;                     // per one-warp CTA, >= 4p
 constexpr int kMidSlots = 8192;                        // per CTA, >= 4p
 // Work (membership tests) per task: a warp-tier task is owned by one warp
-// and groups vertices up to about kWarpWork units, a vertex weighing its
+// and groups vertices up to about warp_work units, a vertex weighing its
 // tests plus kVertexCost (its setup is a chain of dependent loads); each
-// vertex has <= kWarpWork tests, so a task has < 2 kWarpWork tests.  A
-// mid or large vertex is cut into pieces of piece_work(tier, p) tests
-// shared by a CTA.
-constexpr uint64_t kWarpWork = 1u << 12;
+// vertex has <= warp_work tests, so a task has < 2 warp_work tests.  A
+// narrow, mid or large vertex is cut into pieces of piece_work(tier, p)
+// tests, each run by one CTA.
+constexpr uint64_t kWarpWorkMax = 1u << 12;
 constexpr uint64_t kVertexCost = 256;
-constexpr uint64_t kMidPiece = 1u << 16;
-constexpr uint64_t kPieceWork = 1u << 16;
-constexpr uint64_t kPieceMax = 1u << 18;
-__host__ __device__ inline uint64_t piece_work(int tier, uint64_t p) {
-  if (tier == 2) return kMidPiece;
-  uint64_t w = 4 * p;
-  w = w < kPieceWork ? kPieceWork : w;
-  return w > kPieceMax ? kPieceMax : w;
+
+// Run-time choices of the work split (tl_tuning in the C ABI).
+struct Tuning {
+  uint32_t warp_work;    // warp-tier task size, tests (256 .. kWarpWorkMax)
+  uint32_t narrow_piece; // tests per piece of a narrow vertex
+  uint32_t mid_piece;    // tests per piece of a mid vertex
+  uint32_t large_per_p;  // large pieces: clamp(large_per_p * p, large_min, large_max)
+  uint32_t large_min;
+  uint32_t large_max;
+};
+__host__ __device__ inline uint64_t piece_work(const Tuning &tu, int tier, uint64_t p) {
+  if (tier == kTierNarrow) return tu.narrow_piece;
+  if (tier == kTierMid) return tu.mid_piece;
+  uint64_t w = (uint64_t)tu.large_per_p * p;
+  w = w < tu.large_min ? tu.large_min : w;
+  return w > tu.large_max ? tu.large_max : w;
 }
 // Shared-memory probe structures of the large kernel.
 constexpr uint32_t kBitmapMaxN = 1u << 20;               // 128 KiB bitmap over ranks
@@ -48,13 +61,15 @@ constexpr uint32_t kGHashSlots = 1u << 18;
 // (one step adds at most kWarpStep hits) and at the end of its range.
 constexpr uint32_t kWarpBuf = 352;  // 4 mid CTAs (56 KiB each) per SM
 constexpr uint32_t kWarpStep = 128;
+constexpr int kNarrowProbeBytes = kNarrowSlots * 4;
 constexpr int kMidProbeBytes = kMidSlots * 4;
 constexpr int kLargeProbeBytes = (int)(kBitmapMaxN / 8);  // = kHashMaxSlots * 4 = kFilterWords * 4
+constexpr int kNarrowSmemBytes = kNarrowProbeBytes + (kNarrowThreads / 32) * (int)kWarpBuf * 8;
 constexpr int kMidSmemBytes = kMidProbeBytes + (kMidThreads / 32) * (int)kWarpBuf * 8;
 constexpr int kLargeSmemBytes = kLargeProbeBytes + (kLargeThreads / 32) * (int)kWarpBuf * 8;
 // Triangles a warp-tier task can produce (bounded by its work): the size of
 // each warp's global slab.  A chunk must hold at least that many.
-constexpr uint64_t kSlabCapWarp = 2 * kWarpWork;
+constexpr uint64_t kSlabCapWarp = 2 * kWarpWorkMax;
 constexpr uint64_t kSlabCap = kSlabCapWarp;
 __host__ __device__ inline uint64_t slab_cap(int tier) { return tier < 2 ? kSlabCapWarp : 0; }
 
@@ -103,11 +118,13 @@ struct ListArgs {
   const uint64_t *tier_wp;
   const uint32_t *task_start;
   uint64_t tier_count;
-  // mid / large tier: piece prefix over x in [x_begin, x_end) [nr+1] and the
-  // vertex of every task [n_tasks]
+  // narrow / mid / large tier: piece prefix over x in [x_begin, x_end) [nr+1]
+  // and the vertex of every task [n_tasks]; CTAs take tasks from the last
+  // (highest ranks, the largest vertices under a degree ordering) down
   const uint64_t *piece_prefix;
   const uint32_t *task_x;
   uint32_t *ghash;               // large tier, n > kBitmapMaxN: kGHashSlots per CTA (or null)
+  Tuning tu;                     // the work split the task tables were built with
   int tier;
   ListCtl *ctl;
   uint32_t *chunk;               // output chunk, 3 uint32 per triangle
@@ -126,23 +143,24 @@ struct ListArgs {
 void launch_seed_work(const uint32_t *sadj, uint64_t m, const uint64_t *scan_off, uint32_t *w,
                       cudaStream_t s);
 // Per x in [x_begin, x_end): weight in tier 0 / 1 (0 if not in the tier),
-// the membership flags, and the piece counts of tiers 2 and 3.
+// the membership flags, and the piece counts of tiers 2, 3 and 4.
 void launch_classify(const uint64_t *poff, const uint64_t *soff, const uint64_t *WP,
-                     uint32_t x_begin, uint32_t x_end,
+                     uint32_t x_begin, uint32_t x_end, const Tuning &tu,
                      uint64_t *w0, uint64_t *w1, uint32_t *f0, uint32_t *f1, uint64_t *pieces2,
-                     uint64_t *pieces3, cudaStream_t s);
+                     uint64_t *pieces3, uint64_t *pieces4, cudaStream_t s);
 // Compact the vertices of one warp tier: x_list[pos[r]] = x, wp_list[pos[r]] = pref[r].
 void launch_compact_tier(const uint32_t *flags, const uint64_t *pos, const uint64_t *pref,
                          uint32_t x_begin, uint64_t nr, uint32_t *x_list, uint64_t *wp_list,
                          cudaStream_t s);
-// task_start[t] = first tier vertex whose work prefix is >= t * kWarpWork
+// task_start[t] = first tier vertex whose work prefix is >= t * warp_work
 // (clamped to count), t in [0, n_tasks].
 void launch_task_bounds(const uint64_t *wp_list, uint64_t count, uint64_t n_tasks,
-                        uint32_t *task_start, cudaStream_t s);
-// task_x[t] = the vertex owning task t of a mid or large tier.
+                        uint64_t warp_work, uint32_t *task_start, cudaStream_t s);
+// task_x[t] = the vertex owning task t of a narrow, mid or large tier.
 void launch_task_owner(const uint64_t *piece_prefix, uint32_t x_begin, uint64_t nr,
                        uint32_t *task_x, cudaStream_t s);
-// tier 0, 1: warp kernels; tier 2: mid CTA kernel; tier 3: large CTA kernel.
+// tier 0, 1: warp kernels; tier 2: narrow (one-warp) CTA kernel; tier 3: mid
+// CTA kernel; tier 4: large CTA kernel.
 void launch_list(int tier, const ListArgs &a, cudaStream_t s);
 int tier_grid(int tier);
 // Device bytes one listing call holds whatever the graph: two output chunks,

@@ -27,6 +27,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "hash.cuh"
 
 namespace {
 
@@ -37,12 +38,6 @@ static_assert(kNoallocBlocks * kNoallocPerBlock == TL_NOALLOC_MAX_TRIPLES,
               "the header's limit must match the scratch layout");
 
 static __device__ __align__(256) unsigned long long g_noalloc_partials[kNoallocBlocks];
-
-__device__ __forceinline__ uint64_t nz_mix64(uint64_t z) {
-  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
-  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
-  return z ^ (z >> 31);
-}
 
 __device__ __forceinline__ unsigned long long block_sum(unsigned long long v) {
   __shared__ unsigned long long warp_sums[kNoallocThreads / 32];
@@ -64,16 +59,11 @@ __device__ __forceinline__ unsigned long long block_sum(unsigned long long v) {
 __global__ void __launch_bounds__(kNoallocThreads)
     k_noalloc_partials(const uint32_t *__restrict__ t, uint64_t n,
                        unsigned long long *__restrict__ partials) {
-  const uint64_t G = 0x9e3779b97f4a7c15ull;
   const uint64_t begin = (uint64_t)blockIdx.x * kNoallocPerBlock;
   const uint64_t end = (begin + kNoallocPerBlock < n) ? begin + kNoallocPerBlock : n;
   unsigned long long h = 0;
-  for (uint64_t i = begin + threadIdx.x; i < end; i += kNoallocThreads) {
-    uint64_t v = nz_mix64((uint64_t)t[3 * i] + G);
-    v = nz_mix64(v + (uint64_t)t[3 * i + 1] + G);
-    v = nz_mix64(v + (uint64_t)t[3 * i + 2] + G);
-    h += v;
-  }
+  for (uint64_t i = begin + threadIdx.x; i < end; i += kNoallocThreads)
+    h += tl::triple_hash(t[3 * i], t[3 * i + 1], t[3 * i + 2]);
   h = block_sum(h);
   if (threadIdx.x == 0) partials[blockIdx.x] = h;
 }

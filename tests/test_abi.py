@@ -83,3 +83,12 @@ def test_union_and_server_arguments_rejected_without_gpu(built):
     assert built.tl_server_create(ctypes.byref(h), None) == tl.TL_EINVAL
     built.tl_server_free(None)
     assert built.tl_count_hash_parts(None, 0, 0, None) != 0
+
+
+def test_tuning_defaults_and_argument_checks_without_gpu(built):
+    t = tl.tl_default_tuning()
+    assert t == {"warp_work": 4096, "narrow_piece": 1 << 14, "mid_piece": 1 << 16,
+                 "large_per_p": 64, "large_min": 1 << 16, "large_max": 1 << 22}
+    assert built.tl_set_tuning(None, None) == tl.TL_EINVAL
+    out = tl.Tuning()
+    assert built.tl_get_tuning(None, ctypes.byref(out)) == tl.TL_EINVAL

@@ -244,7 +244,7 @@ def test_union_many_parts_every_tier():
     u.order_apply(rank_u)
     vb = _vbase(sizes)
     rank_np = rank_u.cpu().numpy().astype(np.int64)
-    seen = np.zeros(4, np.int64)
+    seen = np.zeros(tl.TL_KERNELS, np.int64)
     for alg in (tl.TL_APP, tl.TL_APM, tl.TL_AMM):
         nt, c, h, probes = u.list_count_hash_parts(alg, sizes)
         seen += np.array(tl.tl_last_list_stats(u.h)["tasks"]) > 0

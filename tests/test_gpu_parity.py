@@ -260,8 +260,9 @@ def test_count_hash_any_alignment_and_length(offset):
 
 def test_every_tier_runs_and_matches():
     """Chung-Lu graph plus a wheel (hub joined to a 5000-cycle): probe sets of
-    every size, so all four listing kernels (small, medium, mid, large with
-    the shared-memory bitmap) get tasks; full set compare with the oracle."""
+    every size, so all five listing kernels (small, medium, narrow, mid,
+    large with the shared-memory bitmap) get tasks; full set compare with the
+    oracle."""
     n = 60000
     base = synth.chung_lu(n, 24, 2.1, 21)
     k = 5000
@@ -270,7 +271,7 @@ def test_every_tier_runs_and_matches():
                     np.r_[np.arange(2, k + 1), 1].astype(np.uint32)], 1)
     e = np.concatenate([base, spokes, rim])
     off, adj = synth.simple_csr(n, e)
-    seen = np.zeros(4, dtype=np.int64)
+    seen = np.zeros(tl.TL_KERNELS, dtype=np.int64)
     g = tl.Graph(n, _dev(e))
     ref = oracle.Graph(n, e)
     for name, rank in [("degree", synth.order_degree(off)), ("identity", synth.order_identity(n)),
@@ -383,3 +384,33 @@ def test_device_generator_on_gpu_matches_host():
     e = synth.chung_lu(50000, 20, 2.2, 4)
     t = dev.chung_lu_device(50000, 20, 2.2, 4, device="cuda", block=1 << 16)
     assert np.array_equal(e, t.cpu().numpy().view(np.uint32))
+
+
+@pytest.mark.parametrize("tuning", [
+    {"warp_work": 256, "narrow_piece": 1024, "mid_piece": 1024, "large_per_p": 1,
+     "large_min": 1024, "large_max": 1024},
+    {"warp_work": 1024, "narrow_piece": 1 << 20, "mid_piece": 1 << 22, "large_per_p": 4096,
+     "large_min": 1 << 16, "large_max": 1 << 26},
+])
+def test_tuning_changes_speed_not_results(tuning):
+    """The work split (tl_set_tuning) changes task shapes only: extreme piece
+    sizes and warp-task sizes list the oracle's triangle set with probes =
+    C++ / C+- / C-- (Property 1)."""
+    n = 30000
+    e = np.concatenate([synth.chung_lu(n, 30, 2.1, 31), synth.complete(90)])
+    rank = synth.order_degree(synth.simple_csr(n, e)[0])
+    g = tl.Graph(n, _dev(e))
+    g.order_apply(_dev(rank))
+    ref = oracle.Graph(n, e)
+    ref.order_apply(rank)
+    tl.tl_set_tuning(g.h, tuning)
+    assert tl.tl_get_tuning(g.h) == tuning
+    for alg in (tl.TL_APP, tl.TL_APM, tl.TL_AMM):
+        t, nt, probes, _ = g.list_collect(alg, tl.TL_MIN_CHUNK_BYTES)
+        rt, rc, rh, rp = ref.list(alg)
+        assert (nt, probes) == (rc, rp), alg
+        assert probes == g.cost(alg), alg
+        assert np.array_equal(oracle.canonical(t), oracle.canonical(rt)), alg
+    tl.tl_set_tuning(g.h, None)
+    assert tl.tl_get_tuning(g.h) == tl.tl_default_tuning()
+    g.free()

@@ -3,10 +3,11 @@ allocate device memory (a consumer runs while the next listing kernel is in
 flight; callers that own all device memory through their own pool cannot
 let it call cudaMalloc there).
 
-Checked against the allocating consumer tl_count_hash on the same device
-buffers, through the C ABI, on two calls in a row (the second with fewer
-triples, so stale partials left in the shared scratch would show), and as
-the consumer of a real listing.  This file sorts last so that a run which
+Checked against the allocating consumer tl_count_hash and against the CPU
+oracle's hash of the same triples (host copies), through the C ABI, on two
+calls in a row (the second with fewer triples, so stale partials left in the
+shared scratch would show), and as the consumer of a real listing, whose
+count and hash are the oracle's.  This file sorts last so that a run which
 stops at the first failure has already run every other test.
 """
 import ctypes
@@ -59,6 +60,9 @@ def test_matches_allocating_consumer_two_calls_in_a_row(env):
         out = torch.zeros(2, dtype=torch.int64, device="cuda")
         got = _noalloc_consumer(tl, torch, buf.data_ptr(), n, out)
         assert (int(got[0]), int(got[1])) == want
+        import oracle
+        host = buf.cpu().numpy().view(np.uint32)
+        assert int(got[1]) == oracle.hash_triples(host) and int(got[0]) == n
 
 
 def test_rejects_more_than_the_maximum(env):
@@ -79,6 +83,8 @@ def test_as_the_consumer_of_a_listing(env):
     e = synth.complete(n)
     gph = tl.Graph(n, torch.from_numpy(e).cuda())
     gph.order_apply(torch.from_numpy(synth.order_random(n, 5)).cuda())
+    import oracle
+    _, ref_cnt, ref_hash, _ = oracle.Graph(n, e).list(oracle.APP, store=False)
     for alg in (tl.TL_APP, tl.TL_APM):
         nt, cnt, h, _ = gph.list_count_hash(alg, tl.TL_MIN_CHUNK_BYTES)
         out = torch.zeros(2, dtype=torch.int64, device="cuda")
@@ -88,5 +94,5 @@ def test_as_the_consumer_of_a_listing(env):
                                    ctypes.cast(ctypes.pointer(st), ctypes.c_void_p))
         got = out.cpu().numpy().astype(np.uint64)
         assert nt2 == nt == cnt == int(got[0]) == n * (n - 1) * (n - 2) // 6
-        assert int(got[1]) == h
+        assert int(got[1]) == h == ref_hash and cnt == ref_cnt
     gph.free()
