@@ -104,17 +104,71 @@ def _draw_from_cdf(cdf: np.ndarray, seed: int, stream: int, count: int,
     return out
 
 
+# ---- arithmetic that gives the same bits on every machine -------------------
+#
+# Library routines for log, exp and pow may differ in their last bit between
+# machines (numpy's vectorised float64 pow does on AVX-512 hosts), and a
+# one-bit change of a Chung-Lu weight moves draws that fall on a bin edge,
+# so the same seed would give slightly different graphs on the host that
+# writes stored results and on the GPU machine.  These versions use only
+# correctly rounded IEEE operations (+, -, *, /, exact frexp / ldexp / rint),
+# one numpy ufunc at a time, in a fixed order; they are accurate to a few
+# units in the last place and, above all, reproducible.
+
+_LN2 = 0.6931471805599453
+
+
+def det_log(x: np.ndarray) -> np.ndarray:
+    """Natural logarithm of positive float64 values: x = m 2^k with m in
+    [sqrt(1/2), sqrt(2)), ln m = 2 atanh(s), s = (m - 1) / (m + 1), summed as
+    an odd series (|s| < 0.172, 14 terms reach double precision)."""
+    x = np.asarray(x, dtype=np.float64)
+    m, k = np.frexp(x)  # x = m 2^k, m in [0.5, 1)
+    low = m < 0.7071067811865476
+    m = np.where(low, m * 2.0, m)
+    k = np.where(low, k - 1, k).astype(np.float64)
+    s = (m - 1.0) / (m + 1.0)
+    s2 = s * s
+    acc = np.full_like(s, 1.0 / 29.0)
+    for j in range(27, 0, -2):  # Horner over 1/29, 1/27, ..., 1/1
+        acc = acc * s2
+        acc = acc + 1.0 / j
+    return k * _LN2 + 2.0 * s * acc
+
+
+def det_exp(y: np.ndarray) -> np.ndarray:
+    """exp of float64 values in a moderate range: y = q ln2 + r with q an
+    integer and |r| <= ln2 / 2, exp r by its Taylor series (18 terms), then
+    scaled by 2^q exactly."""
+    y = np.asarray(y, dtype=np.float64)
+    q = np.rint(y / _LN2)
+    r = y - q * _LN2
+    acc = np.full_like(r, 1.0)
+    for j in range(18, 0, -1):  # Horner: 1 + r/1 (1 + r/2 (1 + ... (1 + r/18)))
+        acc = acc * r
+        acc = acc / j
+        acc = acc + 1.0
+    return np.ldexp(acc, q.astype(np.int64))
+
+
+def det_pow(x: np.ndarray, e: float) -> np.ndarray:
+    """x^e for positive x as exp(e ln x), reproducible bit for bit."""
+    return det_exp(det_log(x) * float(e))
+
+
 def chung_lu_weights(n: int, avg_deg: float, gamma: float) -> np.ndarray:
     """Expected-degree weights w_i proportional to (i+1)^(-1/(gamma-1)).
 
     Scaled so that sum(w) = n * avg_deg, then capped at sqrt(sum(w)) (the
     cap keeps every expected edge probability w_i w_j / sum(w) at most 1).
-    The capped weights are not rescaled.
+    The capped weights are not rescaled.  The power is det_pow and the sums
+    are sequential (np.cumsum), so the weights are the same bits on every
+    machine.
     """
     i = np.arange(n, dtype=np.float64)
-    w = np.power(i + 1.0, -1.0 / (gamma - 1.0))
-    w *= (n * avg_deg) / w.sum()
-    cap = math.sqrt(w.sum())
+    w = det_pow(i + 1.0, -1.0 / (gamma - 1.0))
+    w *= (n * avg_deg) / np.cumsum(w)[-1]
+    cap = math.sqrt(np.cumsum(w)[-1])
     np.minimum(w, cap, out=w)
     return w
 
@@ -144,8 +198,8 @@ def chung_lu_family(count: int, n_range: tuple[int, int], deg_range: tuple[float
     and a distinct edge seed per graph (all from the counter generator under
     ``seed``, streams 10-12).  Graph i is ``chung_lu(n[i], deg[i], gamma[i],
     seeds[i])``."""
-    lo, hi = np.log(n_range[0]), np.log(n_range[1])
-    n = np.rint(np.exp(lo + (hi - lo) * counter_uniform(seed, 10, count))).astype(np.int64)
+    lo, hi = det_log(np.array([float(n_range[0]), float(n_range[1])]))
+    n = np.rint(det_exp(lo + (hi - lo) * counter_uniform(seed, 10, count))).astype(np.int64)
     n = np.clip(n, n_range[0], n_range[1])
     deg = deg_range[0] + (deg_range[1] - deg_range[0]) * counter_uniform(seed, 11, count)
     gam = gamma_range[0] + (gamma_range[1] - gamma_range[0]) * counter_uniform(seed, 12, count)

@@ -46,12 +46,17 @@ def log(*a):
     print(f"[{time.strftime('%H:%M:%S')}]", *a, file=sys.stderr, flush=True)
 
 
-def list_parallel(g, alg, n, threads, parts=4096):
+def list_parallel(g, alg, n, threads, weight, parts=4096):
     """(count, hash, probes) of the whole listing as the sum over disjoint
-    seed-rank ranges; the ranges at the top of the rank space (the hubs,
-    which carry most of the work under the degree ordering) go first."""
-    cuts = np.linspace(0, n, parts + 1).astype(np.int64).tolist()
-    ranges = list(zip(cuts, cuts[1:]))[::-1]
+    seed-rank ranges.  The ranges hold about equal shares of `weight` (a
+    per-rank estimate of the work) and the heaviest go first, so that no
+    single range keeps one thread busy after the others are done."""
+    cum = np.cumsum(weight, dtype=np.float64)
+    cuts = np.searchsorted(cum, np.linspace(0, cum[-1], parts + 1)[1:-1], side="right")
+    cuts = np.unique(np.concatenate([[0], cuts, [n]])).astype(np.int64)
+    ranges = list(zip(cuts[:-1].tolist(), cuts[1:].tolist()))
+    share = [cum[b - 1] - (cum[a - 1] if a else 0.0) for a, b in ranges]
+    ranges = [r for _, r in sorted(zip(share, ranges), reverse=True)]
     done = [0]
     t0 = time.time()
 
@@ -59,7 +64,7 @@ def list_parallel(g, alg, n, threads, parts=4096):
         out = g.list(alg, oracle.LITERAL, int(r[0]), int(r[1]), store=False)
         done[0] += 1
         if done[0] % 256 == 0:
-            log(f"  alg {alg}: {done[0]}/{parts} ranges, {time.time() - t0:.0f} s")
+            log(f"  alg {alg}: {done[0]}/{len(ranges)} ranges, {time.time() - t0:.0f} s")
         return out[1:]
 
     with ThreadPoolExecutor(threads) as ex:
@@ -89,14 +94,19 @@ def main():
     del e
     m = g.m
     log(f"m = {m}; degree ordering")
-    rank = synth.order_degree_from_degrees(g.degrees())
+    deg = g.degrees()
+    rank = synth.order_degree_from_degrees(deg)
     g.order_apply(rank)
     del rank
+    # per-rank work estimate: under the degree ordering the vertex at rank r
+    # has the r-th smallest degree d, and its work grows about as d^2
+    weight = np.sort(deg).astype(np.float64) ** 2 + 1.0
+    del deg
     c_pp, c_pm = g.cost(oracle.APP), g.cost(oracle.APM)
     log(f"C++ = {c_pp}, C+- = {c_pm}")
     res = {}
     for alg, name in ((oracle.APP, "A++"), (oracle.APM, "A+-")):
-        cnt, hsh, probes, dt = list_parallel(g, alg, n, args.threads)
+        cnt, hsh, probes, dt = list_parallel(g, alg, n, args.threads, weight)
         log(f"{name}: T = {cnt}, H = {hsh:#018x}, probes = {probes}, {dt:.0f} s")
         res[name] = {"triangles": cnt, "hash": f"{hsh:#018x}", "probes": probes,
                      "seconds": round(dt, 1)}
@@ -117,7 +127,7 @@ def main():
         "produced_by": "tests/golden/make_chunglu1e8.py (oracle/ only, literal Algorithms 1 "
                        "and 2 over disjoint seed-rank ranges)",
         "host": {"machine": platform.machine(), "cpus": os.cpu_count(),
-                 "threads": args.threads},
+                 "threads": args.threads, "numpy": np.__version__},
         "seconds_total": round(time.time() - t_all, 1),
     }
     with open(args.out, "w") as f:
