@@ -1,22 +1,33 @@
 #!/usr/bin/env python3
 """Benchmark of the triangle-listing hot path on one GB300 (one JSON line).
 
-Workload: R-MAT scale 20 (1,048,576 vertices), edge factor 16, quadrant
-probabilities (0.57, 0.19, 0.19, 0.05), seed 2; symmetrised, deduplicated,
-loops removed by the library (about 15.7M undirected edges); degree
-ordering (ties by id).  One step runs the whole path once:
-graph_load (a1) -> order_apply (a2-a5: relabel, orient, CSR, cost) ->
-list_triangles A++ and list_triangles A+- (a6-a9), each listing streamed in
-1 GiB chunks to the library's device count + hash consumer.
+Headline workload (the paper's largest scale): a Chung-Lu power-law graph
+with n = 10^8 vertices, exponent 2.2, average degree 40, seed 4 (2 * 10^9
+pairs, about 1.99 * 10^9 undirected edges after cleaning), generated on the
+device, degree ordering (ties by id) computed on the device before timing.
+One step runs the whole path once: graph_load (a1) -> order_apply (a2-a5:
+relabel, orient, CSR, cost) -> list_triangles A++ and list_triangles A+-
+(a6-a9), each listing streamed in 1 GiB chunks to the library's device
+count + hash consumer.
 
 value: triangles listed per second of device time over the timed steps
 (both algorithms list the same T triangles; a step lists 2T).  e2e: the
-same step through the C ABI from pinned host buffers, host<->device copies
-included, wall clock.  roofline: the listing kernels' algorithmic bytes
-4 (C + m) + 12 T per listing over their summed CUDA-event time.
+same step through the C ABI from pinned host buffers (edges and ranks
+copied in every step, the count and hash read back), wall clock.
+roofline: the listing kernels' algorithmic bytes 4 (C + m) + 12 T per
+listing over their summed CUDA-event time.  cpu_baseline: the CPU oracle
+(literal Algorithms 1 and 2, one thread) on a stated sample of seed ranks of
+the same graph and ordering, built in a separate process while the GPU
+runs.
 
---impl reference times the CPU oracle (the paper's Algorithms 1 and 2,
-single thread) on bounded samples of the same workload.
+With no --workload the line also carries the other workloads as
+sub-objects: "rmat20" (R-MAT scale 20, with the per-ordering cost-vs-time
+sweep), "batch4096" (4,096 graphs: one disjoint-union pass vs one pass per
+graph) and "serve" (Poisson request stream: batched vs one request per
+pass).  --workload X runs one of them alone as the line's headline.
+
+--impl reference times the CPU oracle as the reference arm on the headline
+workload (the reference is a paper; the oracle stands in for its code).
 """
 from __future__ import annotations
 
@@ -36,50 +47,461 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-WORKLOAD = {"workload": "rmat20-degree", "generator": "R-MAT", "scale": 20, "edge_factor": 16,
-            "abcd": [0.57, 0.19, 0.19, 0.05], "seed": 2, "ordering": "degree (ties by id)",
-            "algorithms": ["A++", "A+-"]}
-DEFAULT_CHUNK_MB = 1024
 METRIC = "triangles/s"
+DEFAULT_CHUNK_MB = 1024
 FALLBACK_HBM_GBS = 6800.0
 NOMINAL_HBM_GBS = 8000.0  # the nominal HBM3e figure, reported beside the measured one
+CHUNK_BYTES = DEFAULT_CHUNK_MB << 20
+
+WORKLOADS = {
+    "chunglu1e8": {"workload": "chunglu1e8-degree", "generator": "Chung-Lu", "n": 100_000_000,
+                   "avg_degree": 40, "exponent": 2.2, "seed": 4,
+                   "ordering": "degree (ties by id), computed on the device",
+                   "algorithms": ["A++", "A+-"]},
+    "rmat20": {"workload": "rmat20-degree", "generator": "R-MAT", "scale": 20, "edge_factor": 16,
+               "abcd": [0.57, 0.19, 0.19, 0.05], "seed": 2, "ordering": "degree (ties by id)",
+               "algorithms": ["A++", "A+-"]},
+}
+DATA = {"Chung-Lu": "synthetic (seeded Chung-Lu power-law graph generated on the device; the "
+                    "paper's datasets are not available)",
+        "R-MAT": "synthetic (seeded R-MAT; the paper's datasets are not available)"}
+
+# The oracle sample of a workload: seed ranks [k n/16, k n/16 + n/(16 S)) for
+# k = 0..15, both algorithms, literal form, one thread.  S is chosen per
+# workload for about 1-3 s of CPU work per sample; cpu_baseline repeats the
+# sample, the reference arm times one sample per step.
+ORACLE_SAMPLE_DIV = {"chunglu1e8": 2048, "rmat20": 64}
 
 
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
-def gen_inputs():
-    from paper_2203_04774_gb300 import synth
-    e = synth.rmat(WORKLOAD["scale"], WORKLOAD["edge_factor"], *WORKLOAD["abcd"][:3],
-                   WORKLOAD["seed"])
-    n = 1 << WORKLOAD["scale"]
-    deg = synth.simple_degrees(n, e)
-    rank = synth.order_degree_from_degrees(deg)
-    return n, e, rank
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
 
 
-def gen_inputs_device(torch, tl):
-    from paper_2203_04774_gb300.synth import device as dev
-    n = WORKLOAD["n"]
-    e = dev.chung_lu_device(n, WORKLOAD["avg_degree"], WORKLOAD["exponent"], WORKLOAD["seed"])
-    g = tl.tl_graph_load(n, e)
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
-        rank = torch.empty(n, dtype=torch.int32, device="cuda")
-        tl.tl_order_compute(g, tl.TL_ORDER_DEGREE, rank)
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def code_only(src: str) -> str:
+    """C++ source without comments, blank lines and trailing spaces."""
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    return "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
+
+
+def list_source_hash():
+    """Hash of the listing kernels' code (list.cu + list.cuh, comments ignored):
+    recorded DRAM counters are used only while it matches."""
+    h = hashlib.sha256()
+    for f in ("list.cu", "list.cuh"):
+        with open(os.path.join(ROOT, "paper_2203_04774_gb300", "csrc", f)) as fh:
+            h.update(code_only(fh.read()).encode())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload: str):
+    """DRAM bytes per step of the listing kernels from the committed ncu
+    summary of this workload, if it was taken on the current listing kernels
+    (else None).  A summary of a smaller case of the same workload scales to
+    the full one by its stated factor."""
+    p = os.path.join(ROOT, "profiles", f"list_{workload}_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        if d.get("list_source_sha256_16") != list_source_hash():
+            return None
+        return int(d["dram_bytes_per_step"] * d.get("scale_to_workload", 1.0))
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+        self.out = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+            if self.out:
+                self.out.close()
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ---- the CPU oracle: sampled listing (cpu_baseline and the reference arm) ----
+
+def sample_ranges(n: int, div: int):
+    """Seed-rank ranges [k n/16, k n/16 + n/(16 div)), k = 0..15."""
+    step = n // 16
+    width = max(1, step // div)
+    return [(k * step, k * step + width) for k in range(16)]
+
+
+def host_inputs(key: str, threads: int = 1):
+    """(n, raw edge pairs, degree-ordering ranks) of a workload on the host,
+    from the same seeded generators as the device path."""
+    from paper_2203_04774_gb300 import synth
+    wl = WORKLOADS[key]
+    if wl["generator"] == "R-MAT":
+        e = synth.rmat(wl["scale"], wl["edge_factor"], *wl["abcd"][:3], wl["seed"])
+        n = 1 << wl["scale"]
+        return n, e, synth.order_degree_from_degrees(synth.simple_degrees(n, e))
+    n = wl["n"]
+    e = synth.chung_lu(n, wl["avg_degree"], wl["exponent"], wl["seed"], threads=threads)
+    return n, e, None
+
+
+def oracle_graph(key: str, threads: int = 1):
+    """The oracle's graph of a workload under the degree ordering, and the
+    seconds taken to draw, load and order it."""
+    import oracle
+    from paper_2203_04774_gb300 import synth
+    t0 = time.perf_counter()
+    n, e, rank = host_inputs(key, threads)
+    g = oracle.Graph(n, e)
+    del e
+    if rank is None:  # degrees of the cleaned graph, then the degree ordering
+        rank = synth.order_degree_from_degrees(g.degrees())
+    g.order_apply(rank)
+    return g, n, time.perf_counter() - t0
+
+
+def oracle_sample(g, n: int, div: int) -> int:
+    """One sample: both algorithms (literal form) over the sample ranges;
+    returns the triangles listed."""
+    import oracle
+    tri = 0
+    for alg in (oracle.APP, oracle.APM):
+        for a, b in sample_ranges(n, div):
+            tri += g.list(alg, oracle.LITERAL, a, b, store=False)[1]
+    return tri
+
+
+def sample_text(key: str, div: int) -> str:
+    return (f"CPU oracle, Algorithms 1 and 2 in the literal boolean-array form, one thread, "
+            f"seed ranks [k n/16, k n/16 + n/{16 * div}) for k = 0..15 ({1 / div:.4g} of the "
+            f"seed vertices) of the {WORKLOADS[key]['workload']} graph under the same degree "
+            f"ordering; listing only (the graph is built first, untimed)")
+
+
+def cpu_baseline_of(g, n: int, key: str, min_s: float = 10.0) -> dict:
+    div = ORACLE_SAMPLE_DIV[key]
+    tri, reps = 0, 0
+    t0 = time.perf_counter()
+    while reps == 0 or time.perf_counter() - t0 < min_s:
+        tri += oracle_sample(g, n, div)
+        reps += 1
+    dt = time.perf_counter() - t0
+    return {"value": tri / dt, "unit": "triangles/s", "cores": 1, "kind": "oracle",
+            "sample": sample_text(key, div) + f"; {reps} samples, {tri} triangles in {dt:.1f} s"}
+
+
+def _oracle_worker(conn, key: str, threads: int):
+    """Runs in a spawned process: build the oracle's graph of the workload
+    (on the host, while the GPU runs), time the sample, send the result."""
+    try:
+        g, n, build_s = oracle_graph(key, threads)
+        res = cpu_baseline_of(g, n, key)
+        res["build_s"] = round(build_s, 1)
+        conn.send(res)
+    except BaseException as ex:  # report, never hang the parent
+        conn.send({"unavailable": f"oracle worker failed: {type(ex).__name__}: {ex}"})
     finally:
-        tl.tl_graph_free(g)
-    return n, e, rank
+        conn.close()
 
 
-WORKLOADS = {
-    "rmat20": WORKLOAD,
-    "chunglu1e8": {"workload": "chunglu1e8-degree", "generator": "Chung-Lu", "n": 100_000_000,
-                   "avg_degree": 40, "exponent": 2.2, "seed": 4,
-                   "ordering": "degree (ties by id), computed on the device",
-                   "algorithms": ["A++", "A+-"]},
-}
+class OracleWorker:
+    """The headline's cpu_baseline, computed in a spawned process started
+    before the first CUDA call."""
 
+    def __init__(self, key: str, threads: int = 8):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        self.conn, child = ctx.Pipe(duplex=False)
+        self.proc = ctx.Process(target=_oracle_worker, args=(child, key, threads), daemon=True)
+        self.proc.start()
+        child.close()
+
+    def result(self, timeout_s: float = 1800.0) -> dict:
+        t0 = time.time()
+        try:
+            if self.conn.poll(timeout_s):
+                res = self.conn.recv()
+            else:
+                res = {"unavailable": f"oracle worker gave no result within {timeout_s:.0f} s"}
+        except EOFError:
+            res = {"unavailable": "oracle worker exited without a result"}
+        self.proc.join(timeout=10)
+        if self.proc.is_alive():
+            self.proc.kill()
+        res["waited_s"] = round(time.time() - t0, 1)
+        return res
+
+
+def run_reference(args, key: str):
+    """The reference arm: the CPU oracle, one sample of the workload per
+    step, on rank 0 only."""
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    g, n, build_s = oracle_graph(key, threads=os.cpu_count() or 1)
+    div = ORACLE_SAMPLE_DIV[key]
+    for _ in range(args.warmup):
+        oracle_sample(g, n, div)
+    t0 = time.perf_counter()
+    tri = sum(oracle_sample(g, n, div) for _ in range(args.steps))
+    dt = time.perf_counter() - t0
+    value = tri / dt
+    wl = WORKLOADS[key]
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "triangles/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": DATA[wl["generator"]],
+        "config": dict(wl, n=n, m=g.m, chunk_bytes=CHUNK_BYTES,
+                       l2="CPU run (no L2 flush)", oracle_build_s=round(build_s, 1)),
+        "cpu_baseline": {"value": value, "unit": "triangles/s", "cores": 1, "kind": "oracle",
+                         "sample": sample_text(key, div) + "; one sample per step"},
+        "e2e": {"value": value, "unit": "triangles/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}), flush=True)
+
+
+# ---- one listing workload: load + order + A++ + A+- per step ------------------
+
+def run_listing(args, key: str, steps: int, warmup: int, e2e: bool, orderings: bool,
+                cpu: str | None, dist=None) -> dict:
+    """Time `steps` whole-path steps of a workload; returns its JSON line.
+    cpu: None (no baseline), "inline" (oracle timed here, after the GPU
+    work) or an OracleWorker's result dict."""
+    import torch
+
+    import paper_2203_04774_gb300 as tl
+    from paper_2203_04774_gb300.synth import device as sdev
+
+    world, rank, local = dist_setup()
+    wl = WORKLOADS[key]
+    t0 = time.time()
+    e_host = r_host = None
+    if wl["generator"] == "Chung-Lu":
+        n = wl["n"]
+        e_dev = sdev.chung_lu_device(n, wl["avg_degree"], wl["exponent"], wl["seed"])
+        g = tl.tl_graph_load(n, e_dev)
+        try:
+            r_dev = torch.empty(n, dtype=torch.int32, device="cuda")
+            tl.tl_order_compute(g, tl.TL_ORDER_DEGREE, r_dev)
+        finally:
+            tl.tl_graph_free(g)
+        if e2e:  # the same inputs in pinned host memory
+            e_host = torch.empty(e_dev.shape, dtype=e_dev.dtype, pin_memory=True)
+            e_host.copy_(e_dev)
+            r_host = torch.empty(r_dev.shape, dtype=r_dev.dtype, pin_memory=True)
+            r_host.copy_(r_dev)
+    else:
+        n, e, rnk = host_inputs(key)
+        e_dev = torch.from_numpy(e).cuda()
+        r_dev = torch.from_numpy(rnk.view(np.int32)).cuda()
+        if e2e:
+            e_host = torch.from_numpy(e).pin_memory()
+            r_host = torch.from_numpy(rnk.view(np.int32)).pin_memory()
+    torch.cuda.synchronize()
+    log(f"[bench] {key}: inputs ready in {time.time() - t0:.1f}s: n={n} pairs={e_dev.shape[0]}")
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    # the consumer reduces each chunk on its own stream, overlapping the
+    # listing kernel that fills the other chunk buffer
+    cstream = torch.cuda.Stream()
+    ch = tl.CountHash(cstream.cuda_stream)
+    ch_ptr = tl.tl_count_hash_ptr()
+
+    phase_names = ["graph_load", "order_apply", "list_A++", "list_A+-", "graph_free"]
+    phase_ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(phase_names) + 1)]
+    phase_ms = {k: [] for k in phase_names}
+
+    def step(edges, ranks):
+        phase_ev[0].record(stream)
+        g = tl.tl_graph_load(n, edges, stream.cuda_stream)
+        phase_ev[1].record(stream)
+        try:
+            tl.tl_order_apply(g, ranks)
+            phase_ev[2].record(stream)
+            m = tl.tl_graph_size(g)[1]
+            costs = [tl.tl_cost(g, a) for a in (tl.TL_APP, tl.TL_APM)]
+            out = []
+            for i, a in enumerate((tl.TL_APP, tl.TL_APM)):
+                ch.reset()
+                nt = tl.tl_list_triangles(g, a, CHUNK_BYTES, ch_ptr, ch.user)
+                phase_ev[3 + i].record(stream)
+                out.append((nt, int(ch.state.count), int(ch.state.hash),
+                            tl.tl_last_list_stats(g)))
+            return m, costs, out
+        finally:
+            tl.tl_graph_free(g)
+            phase_ev[5].record(stream)
+            phase_ev[5].synchronize()
+            for i, k in enumerate(phase_names):
+                phase_ms[k].append(phase_ev[i].elapsed_time(phase_ev[i + 1]))
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+
+    for _ in range(warmup):
+        step(e_dev, r_dev)
+    # timed region (device), L2 flushed before every step
+    clocks = Clocks(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    launches0 = tl.tl_kernel_launches()
+    results = []
+    barrier()
+    clocks.start()
+    for i in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        ev[i][0].record(stream)
+        results.append(step(e_dev, r_dev))
+        ev[i][1].record(stream)
+    barrier()
+    clk = clocks.stop()
+    launches = tl.tl_kernel_launches() - launches0
+    timed_phase_ms = {k: statistics.median(v[-steps:]) for k, v in phase_ms.items()}
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    m, costs, out = results[-1]
+    T = out[0][0]
+    assert all(o[0] == T and o[1] == T for r in results for o in r[2]), "triangle counts differ"
+    assert len({o[2] for r in results for o in r[2]}) == 1, "set hashes differ"
+    tri_per_step = sum(o[0] for o in out)
+    value = tri_per_step * steps * world / (total_ms / 1e3)
+
+    # roofline of the listing kernels (both algorithms, all launches)
+    list_ms = statistics.mean(sum(sum(o[3]["kernel_ms"]) for o in r[2]) for r in results)
+    alg_bytes = sum(4 * (c + m) + 12 * T for c in costs)
+    peak, peak_kind = read_peaks()
+    achieved = alg_bytes / (list_ms / 1e3) / 1e9
+
+    # end to end through the C ABI from pinned host buffers
+    e2e_ms = []
+    for _ in range(max(2, min(steps, 5)) if e2e else 0):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        step(e_host, r_host)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t1) * 1e3)
+    e2e_value = tri_per_step * len(e2e_ms) / (sum(e2e_ms) / 1e3) if e2e_ms else None
+
+    per_ordering = None
+    if rank == 0 and orderings:
+        e_np = e_dev.cpu().numpy().view(np.uint32)
+        per_ordering = ordering_sweep(tl, n, e_np, e_dev, stream)
+    ch.release()
+    del e_dev, r_dev, e_host, r_host, flush
+    torch.cuda.empty_cache()
+
+    cpu_res = None
+    if rank == 0 and world == 1 and cpu == "inline":
+        g_or, n_or, _ = oracle_graph(key)
+        cpu_res = cpu_baseline_of(g_or, n_or, key)
+        del g_or
+    elif isinstance(cpu, dict):
+        cpu_res = cpu
+    return {
+        "metric": METRIC, "value": value, "unit": "triangles/s", "n_gpus": world,
+        "steps": steps, "warmup": warmup, "ms_per_step": total_ms / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": DATA[wl["generator"]],
+        "config": dict(wl, n=n, m=m, triangles=T, C_pp=costs[0], C_pm=costs[1],
+                       chunk_bytes=CHUNK_BYTES,
+                       l2="inputs larger than L2, and a 256 MiB buffer written before each step",
+                       parallelism="replicas" if world > 1 else "1 GPU"),
+        "oriented_edges_per_s": m * 2 * steps * world / (total_ms / 1e3),
+        "e2e": {"value": e2e_value, "unit": "triangles/s",
+                "h2d_bytes_per_step": h2d_bytes(key, n) if e2e else None,
+                "d2h_bytes_per_step": 2 * 16},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": recorded_traffic(key),
+                     "nominal_peak": NOMINAL_HBM_GBS,
+                     "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
+                     "kernel": "k_list_warp<64|2048> + k_list_cta<32|256|1024> (A++ and A+-)",
+                     "algorithmic_bytes_per_step": alg_bytes, "kernel_ms_per_step": list_ms,
+                     "compulsory_bytes_per_step": len(costs) * (8 * m + 12 * T),
+                     "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"},
+        "list_stats": {a: r[3] for a, r in zip(("A++", "A+-"), out)},
+        "phase_ms_median": timed_phase_ms,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "cpu_baseline": cpu_res,
+        "per_ordering": per_ordering,
+    }
+
+
+def h2d_bytes(key: str, n: int) -> int:
+    """Host-to-device bytes of one e2e step: the raw pairs and the ranks."""
+    wl = WORKLOADS[key]
+    pairs = (wl["edge_factor"] << wl["scale"]) if wl["generator"] == "R-MAT" else \
+        int(round(wl["n"] * wl["avg_degree"] / 2.0))
+    return pairs * 8 + n * 4
+
+
+# ---- many graphs: batched listing and serving ------------------------------
 
 BATCH = {"workload": "batch4096-chunglu-degree-A++", "generator": "Chung-Lu family",
          "graphs": 4096, "n_range": [1000, 200000], "n_distribution": "log-uniform",
@@ -87,7 +509,7 @@ BATCH = {"workload": "batch4096-chunglu-degree-A++", "generator": "Chung-Lu fami
          "ordering": "degree (ties by id), computed on the device", "algorithms": ["A++"]}
 
 
-def run_batch(args):
+def run_batch(args, steps: int, warmup: int) -> dict:
     """Many independent graphs: one disjoint-union pass vs one pass per graph.
 
     A step takes the 4096 edge lists (device resident) to per-graph triangle
@@ -101,8 +523,6 @@ def run_batch(args):
     from paper_2203_04774_gb300 import synth
     from paper_2203_04774_gb300.synth import device as sdev
 
-    world, rank, local = dist_setup()
-    torch.cuda.set_device(local)
     fam = synth.chung_lu_family(BATCH["graphs"], BATCH["n_range"], BATCH["avg_degree_range"],
                                 BATCH["exponent_range"], BATCH["seed"])
     k = BATCH["graphs"]
@@ -174,19 +594,19 @@ def run_batch(args):
             ms.append((time.perf_counter() - t1) * 1e3)
         return out, ms
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         batched()
-    clocks = Clocks(local)
+    clocks = Clocks(torch.cuda.current_device())
     clocks.start()
     launches0 = tl.tl_kernel_launches()
-    (nt, m, cb, hb, st), b_ms = timed(batched, args.steps)
-    b_launches = (tl.tl_kernel_launches() - launches0) / args.steps
-    per_warm = max(1, min(args.warmup, 1))
+    (nt, m, cb, hb, st), b_ms = timed(batched, steps)
+    b_launches = (tl.tl_kernel_launches() - launches0) / steps
+    per_warm = 1
     for _ in range(per_warm):
         per_graph()
     launches0 = tl.tl_kernel_launches()
-    (nt1, m1, c1, h1, lat), p_ms = timed(per_graph, max(1, min(args.steps, 2)))
-    p_launches = (tl.tl_kernel_launches() - launches0) / max(1, min(args.steps, 2))
+    (nt1, m1, c1, h1, lat), p_ms = timed(per_graph, max(1, min(steps, 2)))
+    p_launches = (tl.tl_kernel_launches() - launches0) / max(1, min(steps, 2))
     clk = clocks.stop()
     assert nt == nt1 and m == m1, (nt, nt1, m, m1)
     assert np.array_equal(cb, c1) and np.array_equal(hb, h1), "per-graph results differ"
@@ -205,8 +625,8 @@ def run_batch(args):
     p_s = statistics.median(p_ms) / 1e3
     line = {
         "metric": "graphs/s (batched disjoint-union pass vs one pass per graph)",
-        "value": k / b_s, "unit": "graphs/s", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": b_s * 1e3, "higher_is_better": True,
+        "value": k / b_s, "unit": "graphs/s", "n_gpus": 1, "steps": steps,
+        "warmup": warmup, "ms_per_step": b_s * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (seeded Chung-Lu family, generated on the device)",
         "config": dict(BATCH, m=m, triangles=nt, pairs=int(po[-1]), vertices=n_all,
@@ -223,11 +643,13 @@ def run_batch(args):
                                     "note": "per graph, run back to back"}},
         "speedup_batched_vs_per_graph": p_s / b_s,
         "equal_output": True, "oracle_spot_check_graphs": len(spot),
-        "gpu_launches": b_launches * args.steps,
+        "gpu_launches": b_launches * steps,
         "clocks": clk,
     }
-    print(json.dumps(line), flush=True)
     ch.release()
+    del e_all, rank_all, flush
+    torch.cuda.empty_cache()
+    return line
 
 
 SERVE = {"workload": "serve-chunglu-poisson", "generator": "Chung-Lu family", "pool_graphs": 128,
@@ -238,7 +660,10 @@ SERVE = {"workload": "serve-chunglu-poisson", "generator": "Chung-Lu family", "p
          "rates_per_s": [100, 1000, 10000], "requests_per_rate": 2000}
 
 
-def run_serve(args):
+SIZE_BUCKETS = [(0, 1e5), (1e5, 1e6), (1e6, 1e7), (1e7, float("inf"))]
+
+
+def run_serve(args, requests: int) -> dict:
     """Poisson stream of listing requests against the request server.
 
     The pool graphs and their orderings are generated, loaded and registered
@@ -255,10 +680,8 @@ def run_serve(args):
     from paper_2203_04774_gb300 import synth
     from paper_2203_04774_gb300.synth import device as sdev
 
-    torch.cuda.set_device(0)
     cfg = dict(SERVE)
-    if args.serve_requests:
-        cfg["requests_per_rate"] = args.serve_requests
+    cfg["requests_per_rate"] = requests
     fam = synth.chung_lu_family(cfg["pool_graphs"], cfg["n_range"], cfg["avg_degree_range"],
                                 cfg["exponent_range"], cfg["seed"])
     t0 = time.time()
@@ -322,9 +745,20 @@ def run_serve(args):
                "requests_per_s": R / span, "triangles_per_s": tri / span,
                "mean_batch": float(np.mean([r["batch_size"] for r in res])),
                "max_batch_seen": int(max(r["batch_size"] for r in res))}
+        # latency by request size (edges of the requested graph)
+        req_m = np.asarray(ms, np.float64)[gi]
+        by_size = []
+        for lo, hi in SIZE_BUCKETS:
+            sel = (req_m >= lo) & (req_m < hi)
+            if sel.any():
+                by_size.append({"edges": [lo, hi if hi < float("inf") else None],
+                                "requests": int(sel.sum()),
+                                "p50_s": float(np.percentile(lat[sel], 50)),
+                                "p99_s": float(np.percentile(lat[sel], 99))})
+        out["by_size"] = by_size
         return out, [(r["triangles"], r["hash"]) for r in res]
 
-    clocks = Clocks(0)
+    clocks = Clocks(torch.cuda.current_device())
     clocks.start()
     launches0 = tl.tl_kernel_launches()
     rows = []
@@ -350,267 +784,10 @@ def run_serve(args):
                        per_request={"max_batch": 1, "workers": 1}),
         "rates": rows, "equal_output": True, "gpu_launches": launches, "clocks": clk,
     }
-    print(json.dumps(line), flush=True)
+    del graphs
+    torch.cuda.empty_cache()
+    return line
 
-
-def read_peaks():
-    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    try:
-        with open(p) as f:
-            d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
-    except Exception:
-        return FALLBACK_HBM_GBS, "fallback"
-
-
-def code_only(src: str) -> str:
-    """C++ source without comments, blank lines and trailing spaces."""
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    src = re.sub(r"//[^\n]*", "", src)
-    return "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
-
-
-def list_source_hash():
-    """Hash of the listing kernels' code (list.cu + list.cuh, comments ignored):
-    recorded DRAM counters are used only while it matches."""
-    h = hashlib.sha256()
-    for f in ("list.cu", "list.cuh"):
-        with open(os.path.join(ROOT, "paper_2203_04774_gb300", "csrc", f)) as fh:
-            h.update(code_only(fh.read()).encode())
-    return h.hexdigest()[:16]
-
-
-def recorded_traffic():
-    """DRAM bytes per listing pass from the committed ncu summary, if it was
-    taken on the current listing kernels (else None)."""
-    p = os.path.join(ROOT, "profiles", "list_rmat20_traffic.json")
-    try:
-        with open(p) as f:
-            d = json.load(f)
-        if d.get("list_source_sha256_16") == list_source_hash():
-            return d.get("dram_bytes_per_step")
-    except Exception:
-        pass
-    return None
-
-
-class Clocks:
-    """nvidia-smi sampling during the timed region."""
-
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-
-    def __init__(self, gpu_index: int):
-        self.gpu = gpu_index
-        self.proc = None
-        self.path = None
-        self.out = None
-
-    def start(self):
-        try:
-            fd, self.path = tempfile.mkstemp(suffix=".csv")
-            os.close(fd)
-            self.out = open(self.path, "w")
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=self.out, stderr=subprocess.DEVNULL)
-        except Exception:
-            self.proc = None
-            if self.out:
-                self.out.close()
-
-    def stop(self):
-        if not self.proc:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except Exception:
-            self.proc.kill()
-        self.out.close()
-        rows = []
-        with open(self.path) as f:
-            for line in f:
-                parts = [x.strip() for x in line.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
-        os.unlink(self.path)
-        if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
-
-
-def dist_setup():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
-
-
-def run_tl(args):
-    import torch
-
-    import paper_2203_04774_gb300 as tl
-
-    world, rank, local = dist_setup()
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    t0 = time.time()
-    if WORKLOAD["generator"] == "Chung-Lu":
-        # too large for the host: edges drawn on the device, degree ordering
-        # computed on the device (both before the timed region)
-        n, e_dev, r_dev = gen_inputs_device(torch, tl)
-        e = rnk = None
-        args.no_cpu = args.no_orderings = args.no_e2e = True
-        npairs = e_dev.shape[0]
-    else:
-        n, e, rnk = gen_inputs()
-        e_dev = torch.from_numpy(e).cuda()
-        r_dev = torch.from_numpy(rnk).cuda()
-        npairs = len(e)
-    log(f"[bench] inputs ready in {time.time() - t0:.1f}s: n={n} pairs={npairs}")
-    stream = torch.cuda.Stream()
-    e_pin = torch.from_numpy(e).pin_memory() if e is not None else None
-    r_pin = torch.from_numpy(rnk).pin_memory() if rnk is not None else None
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    # the consumer reduces each chunk on its own stream, overlapping the
-    # listing kernel that fills the other chunk buffer
-    cstream = torch.cuda.Stream()
-    ch = tl.CountHash(cstream.cuda_stream)
-    ch_ptr = tl.tl_count_hash_ptr()
-
-    phase_names = ["graph_load", "order_apply", "list_A++", "list_A+-", "graph_free"]
-    phase_ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(phase_names) + 1)]
-    phase_ms = {k: [] for k in phase_names}
-
-    def step(edges, ranks):
-        phase_ev[0].record(stream)
-        g = tl.tl_graph_load(n, edges, stream.cuda_stream)
-        phase_ev[1].record(stream)
-        try:
-            tl.tl_order_apply(g, ranks)
-            phase_ev[2].record(stream)
-            m = tl.tl_graph_size(g)[1]
-            costs = [tl.tl_cost(g, a) for a in (tl.TL_APP, tl.TL_APM)]
-            out = []
-            for i, a in enumerate((tl.TL_APP, tl.TL_APM)):
-                ch.reset()
-                nt = tl.tl_list_triangles(g, a, CHUNK_BYTES, ch_ptr, ch.user)
-                phase_ev[3 + i].record(stream)
-                out.append((nt, int(ch.state.count), int(ch.state.hash),
-                            tl.tl_last_list_stats(g)))
-            return m, costs, out
-        finally:
-            tl.tl_graph_free(g)
-            phase_ev[5].record(stream)
-            phase_ev[5].synchronize()
-            for i, k in enumerate(phase_names):
-                phase_ms[k].append(phase_ev[i].elapsed_time(phase_ev[i + 1]))
-
-    def barrier():
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-
-    for _ in range(args.warmup):
-        step(e_dev, r_dev)
-    # timed region (device), L2 flushed before every step
-    clocks = Clocks(local)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    launches0 = tl.tl_kernel_launches()
-    results = []
-    barrier()
-    clocks.start()
-    for i in range(args.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        ev[i][0].record(stream)
-        results.append(step(e_dev, r_dev))
-        ev[i][1].record(stream)
-    barrier()
-    clk = clocks.stop()
-    launches = tl.tl_kernel_launches() - launches0
-    timed_phase_ms = {k: statistics.median(v[-args.steps:]) for k, v in phase_ms.items()}
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    m, costs, out = results[-1]
-    T = out[0][0]
-    assert all(o[0] == T and o[1] == T for r in results for o in r[2]), "triangle counts differ"
-    assert len({o[2] for r in results for o in r[2]}) == 1, "set hashes differ"
-    tri_per_step = sum(o[0] for o in out)
-    value = tri_per_step * args.steps * world / (total_ms / 1e3)
-
-    # roofline of the listing kernels (both algorithms, all launches)
-    list_ms = statistics.mean(sum(sum(o[3]["kernel_ms"]) for o in r[2]) for r in results)
-    alg_bytes = sum(4 * (c + m) + 12 * T for c in costs)
-    peak, peak_kind = read_peaks()
-    achieved = alg_bytes / (list_ms / 1e3) / 1e9
-    traffic = recorded_traffic()
-
-    # end to end through the C ABI from pinned host buffers
-    e2e_ms = []
-    for _ in range(0 if args.no_e2e else max(2, min(args.steps, 5))):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        step(e_pin, r_pin)
-        torch.cuda.synchronize()
-        e2e_ms.append((time.perf_counter() - t1) * 1e3)
-    e2e_value = tri_per_step * len(e2e_ms) / (sum(e2e_ms) / 1e3) if e2e_ms else None
-
-    per_ordering = None
-    if rank == 0 and not args.no_orderings:
-        per_ordering = ordering_sweep(tl, n, e, e_dev, stream)
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(n, e, rnk)
-    ch.release()
-
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": "triangles/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-            "data": "synthetic (seeded R-MAT; the paper's datasets are not available)",
-            "config": dict(WORKLOAD, n=n, m=m, triangles=T, C_pp=costs[0], C_pm=costs[1],
-                           chunk_bytes=CHUNK_BYTES, l2="256 MiB buffer written before each step",
-                           parallelism="replicas" if world > 1 else "1 GPU"),
-            "oriented_edges_per_s": m * 2 * args.steps * world / (total_ms / 1e3),
-            "e2e": {"value": e2e_value, "unit": "triangles/s",
-                    "h2d_bytes_per_step": int(e.nbytes + rnk.nbytes) if e is not None else None,
-                    "d2h_bytes_per_step": 2 * 16},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
-                         "kernel": "k_list_warp<64|2048> + k_list_cta<256,2|1024,3> (A++ and A+-)",
-                         "algorithmic_bytes_per_step": alg_bytes, "kernel_ms_per_step": list_ms,
-                         "compulsory_bytes_per_step": len(costs) * (8 * m + 12 * T),
-                         "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"},
-            "list_stats": {a: r[3] for a, r in zip(("A++", "A+-"), out)},
-            "phase_ms_median": timed_phase_ms,
-            "gpu_launches": launches,
-            "clocks": clk,
-            "cpu_baseline": cpu,
-            "per_ordering": per_ordering,
-        }
-        print(json.dumps(line), flush=True)
-    if dist:
-        dist.destroy_process_group()
 
 
 def ordering_sweep(tl, n, e, e_dev, stream):
@@ -668,67 +845,6 @@ def ordering_sweep(tl, n, e, e_dev, stream):
     return rows
 
 
-def _oracle_sample_ranges(n, parts=16, frac=4):
-    """Seed-rank ranges [k n/parts, k n/parts + n/(parts*frac)): 1/frac of the
-    seed vertices, spread over the whole rank range."""
-    step = n // parts
-    width = max(1, step // frac)
-    return [(k * step, k * step + width) for k in range(parts)]
-
-
-def cpu_baseline(n, e, rnk, frac=4):
-    import oracle
-    g = oracle.Graph(n, e)
-    g.order_apply(rnk)
-    tri = 0
-    t0 = time.perf_counter()
-    for alg in (oracle.APP, oracle.APM):
-        for a, b in _oracle_sample_ranges(n, frac=frac):
-            tri += g.list(alg, oracle.LITERAL, a, b, store=False)[1]
-    dt = time.perf_counter() - t0
-    return {"value": tri / dt, "unit": "triangles/s", "cores": 1, "kind": "oracle",
-            "sample": f"Algorithms 1 and 2 (literal boolean-array form), seed ranks "
-                      f"[k n/16, k n/16 + n/{16 * frac}) for k = 0..15 (1/{frac} of the seed "
-                      f"vertices) of the same graph and degree ordering; listing only, single "
-                      f"thread; {tri} triangles in {dt:.1f} s"}
-
-
-def run_reference(args):
-    world, rank, local = dist_setup()
-    if rank != 0:
-        return
-    import oracle
-    n, e, rnk = gen_inputs()
-    g = oracle.Graph(n, e)
-    g.order_apply(rnk)
-    ranges = _oracle_sample_ranges(n, parts=16, frac=16)
-
-    def step():
-        tri = 0
-        for alg in (oracle.APP, oracle.APM):
-            for a, b in ranges:
-                tri += g.list(alg, oracle.LITERAL, a, b, store=False)[1]
-        return tri
-
-    for _ in range(args.warmup):
-        step()
-    t0 = time.perf_counter()
-    tri = sum(step() for _ in range(args.steps))
-    dt = time.perf_counter() - t0
-    value = tri / dt
-    sample = ("CPU oracle (Algorithms 1 and 2, literal form, single thread) over seed ranks "
-              "[k n/16, k n/16 + n/256), k = 0..15, of R-MAT scale 20 with degree ordering; "
-              "listing only")
-    print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "triangles/s",
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded R-MAT)",
-        "config": dict(WORKLOAD, n=n, m=g.m),
-        "cpu_baseline": {"value": value, "unit": "triangles/s", "cores": 1, "kind": "oracle",
-                         "sample": sample},
-        "e2e": {"value": value, "unit": "triangles/s", "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": 0}}), flush=True)
 
 
 def main():
@@ -737,51 +853,64 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tl", choices=["tl", "reference"])
-    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--workload", default="all",
+                    choices=["all", "chunglu1e8", "rmat20", "batch4096", "serve"],
+                    help="all (default): the 2e9-edge Chung-Lu graph as the headline, with "
+                         "rmat20, batch4096 and serve as sub-objects; or one workload alone")
+    ap.add_argument("--sub-steps", type=int, default=5,
+                    help="timed steps of the rmat20 and batch4096 sub-objects")
+    ap.add_argument("--serve-requests", type=int, default=0,
+                    help="requests per arrival rate (default 2000 as a sub-object, 20000 alone)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baselines")
     ap.add_argument("--no-orderings", action="store_true", help="skip the per-ordering sweep")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
-    ap.add_argument("--scale", type=int, default=20,
-                    help="R-MAT scale (20 is the measured workload; smaller for profiling)")
     ap.add_argument("--chunk-mb", type=int, default=DEFAULT_CHUNK_MB,
                     help="output chunk size in MiB")
-    ap.add_argument("--serve-requests", type=int, default=0,
-                    help="requests per arrival rate in the serve workload (default 2000)")
-    ap.add_argument("--workload", default="rmat20",
-                    choices=sorted(WORKLOADS) + ["batch4096", "serve"],
-                    help="rmat20: the measured workload; chunglu1e8: the 2e9-edge graph; "
-                         "batch4096: 4096 graphs, batched vs one pass per graph; "
-                         "serve: Poisson request stream, batched vs per-request")
     args = ap.parse_args()
-    global CHUNK_BYTES, WORKLOAD
+    global CHUNK_BYTES
     CHUNK_BYTES = args.chunk_mb << 20
-    if args.workload == "serve":
-        if args.impl == "reference":
-            print(json.dumps({"impl": "reference", "unavailable": "the serving workload has no "
-                              "reference arm; its baseline is the per-request mode in the same "
-                              "line"}))
-        else:
-            run_serve(args)
-        return
-    if args.workload == "batch4096":
-        if args.impl == "reference":
-            print(json.dumps({"impl": "reference", "unavailable": "the batched workload has no "
-                              "reference arm; its baseline is the per-graph pass in the same "
-                              "line"}))
-        else:
-            run_batch(args)
-        return
-    WORKLOAD = WORKLOADS[args.workload]
-    if args.scale != 20 and args.workload == "rmat20":
-        WORKLOAD["scale"] = args.scale
-        WORKLOAD["workload"] = f"rmat{args.scale}-degree"
-    if args.impl == "reference" and args.workload != "rmat20":
-        print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle cannot hold the "
-                          "2e9-edge graph; its reference arm runs on rmat20 only"}))
-        return
+    wl = args.workload
     if args.impl == "reference":
-        run_reference(args)
+        if wl in ("batch4096", "serve"):
+            print(json.dumps({"impl": "reference", "unavailable": f"the {wl} workload has no "
+                              "reference arm; its baseline is the unbatched mode in the same "
+                              "line"}))
+            return
+        run_reference(args, "rmat20" if wl == "rmat20" else "chunglu1e8")
+        return
+    world, rank, local = dist_setup()
+    worker = None
+    if wl in ("all", "chunglu1e8") and world == 1 and not args.no_cpu:
+        worker = OracleWorker("chunglu1e8")  # spawned before the first CUDA call
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if wl in ("all", "chunglu1e8"):
+        line = run_listing(args, "chunglu1e8", args.steps, args.warmup, e2e=not args.no_e2e,
+                           orderings=False, cpu=None, dist=dist)
+        if wl == "all" and world == 1:
+            line["rmat20"] = run_listing(args, "rmat20", args.sub_steps, 3, e2e=not args.no_e2e,
+                                         orderings=not args.no_orderings,
+                                         cpu=None if args.no_cpu else "inline")
+            line["batch4096"] = run_batch(args, args.sub_steps, 1)
+            line["serve"] = run_serve(args, args.serve_requests or 2000)
+        if worker:
+            line["cpu_baseline"] = worker.result()
+    elif wl == "rmat20":
+        line = run_listing(args, "rmat20", args.steps, args.warmup, e2e=not args.no_e2e,
+                           orderings=not args.no_orderings,
+                           cpu=None if args.no_cpu or world > 1 else "inline", dist=dist)
+    elif wl == "batch4096":
+        line = run_batch(args, args.steps, args.warmup)
     else:
-        run_tl(args)
+        line = run_serve(args, args.serve_requests or 20000)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
 
 
 if __name__ == "__main__":

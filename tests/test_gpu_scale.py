@@ -1,19 +1,24 @@
 """Full-size listing of the largest configuration: Chung-Lu, n = 10^8 vertices,
 exponent 2.2, average degree 40 (about 2 * 10^9 edges), seed 4, generated on
-the device.
+the device, in the launch configuration of the benchmark (1 GiB chunks, the
+library's count + hash consumer).
 
-The oracle cannot hold this graph, so the CUDA path is checked through
-properties that hold at any size, each computed by independent means:
-  * A++ and A+- (different probe sets, different tiers) list the same number
-    of triangles with the same order-free set hash;
-  * so do two different orderings (degree and Split, both computed on the
-    device), i.e. two different DAGs;
+Compared with the CPU oracle's listing of the same graph
+(tests/golden/chunglu1e8.json, written by tests/golden/make_chunglu1e8.py
+from oracle/ alone): the number of edges after cleaning, the triangle count
+and the 64-bit set hash of A++ and A+- under the degree ordering, and the
+costs C++ and C+- of that ordering, which by Property 1 are also the probe
+counts.  The triangle set does not depend on the ordering, so the Split and
+core orderings (computed on the device) must give the same count and hash.
+Beside that, properties that hold at any size:
   * the membership tests performed equal C++ resp. C+- (Property 1);
   * a sample of listed triangles are triangles of the raw edge list (all
     three edges found in a sorted copy of the input), with a < b < c and no
     duplicates.
 """
 import ctypes
+import json
+import os
 
 import numpy as np
 import pytest
@@ -23,6 +28,14 @@ pytestmark = pytest.mark.gpu
 N, AVG, GAMMA_EXP, SEED = 100_000_000, 40, 2.2, 4
 CHUNK = 1 << 30
 SAMPLE = 1 << 20
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "chunglu1e8.json")
+
+
+def _golden():
+    with open(GOLDEN) as f:
+        d = json.load(f)
+    assert (d["n"], d["avg_degree"], d["exponent"], d["seed"]) == (N, AVG, GAMMA_EXP, SEED)
+    return d
 
 
 @pytest.fixture(scope="module")
@@ -62,15 +75,20 @@ def _list(tl, torch, g, alg, keep_sample=False):
 def test_chung_lu_1e8_vertices_2e9_edges(env):
     tl, torch = env
     from paper_2203_04774_gb300.synth import device as dev
+    gold = _golden()
+    want = (gold["triangles"], int(gold["hash"], 16))
     edges = dev.chung_lu_device(N, AVG, GAMMA_EXP, SEED)
+    assert edges.shape[0] == gold["pairs"]
     g = tl.tl_graph_load(N, edges)
     try:
         n, m = tl.tl_graph_size(g)
-        assert n == N and 1.5e9 < m <= edges.shape[0]
+        assert n == N and m == gold["m"]
         results = {}
         rank = torch.empty(N, dtype=torch.int32, device="cuda")
         tl.tl_order_compute(g, tl.TL_ORDER_DEGREE, rank)
         tl.tl_order_apply(g, rank)
+        assert tl.tl_cost(g, tl.TL_APP) == gold["C_pp"]
+        assert tl.tl_cost(g, tl.TL_APM) == gold["C_pm"]
         for alg in (tl.TL_APP, tl.TL_APM):
             nt, cnt, h, probes, st, smp = _list(tl, torch, g, alg, keep_sample=alg == tl.TL_APP)
             assert probes == tl.tl_cost(g, alg)  # Property 1
@@ -78,21 +96,22 @@ def test_chung_lu_1e8_vertices_2e9_edges(env):
             results[("degree", alg)] = (nt, h)
             if smp is not None:
                 sample = smp
-        tl.tl_order_compute(g, tl.TL_ORDER_SPLIT, rank)
-        tl.tl_order_apply(g, rank)
-        nt, cnt, h, probes, st, _ = _list(tl, torch, g, tl.TL_APM)
-        assert probes == tl.tl_cost(g, tl.TL_APM)
-        results[("split", tl.TL_APM)] = (nt, h)
-        assert len(set(results.values())) == 1, results
-        assert results[("degree", tl.TL_APP)][0] > 1e9
+        for kind, name, alg in ((tl.TL_ORDER_SPLIT, "split", tl.TL_APM),
+                                (tl.TL_ORDER_CORE, "core", tl.TL_APP)):
+            tl.tl_order_compute(g, kind, rank)
+            tl.tl_order_apply(g, rank)
+            nt, cnt, h, probes, st, _ = _list(tl, torch, g, alg)
+            assert probes == tl.tl_cost(g, alg)
+            results[(name, alg)] = (nt, h)
+        for key, got in results.items():
+            assert got == want, (key, got, want)
     finally:
         tl.tl_graph_free(g)
         del rank
     # sampled triangles are triangles of the raw input
     s = sample.to(torch.int64)
     assert bool((s[:, 0] < s[:, 1]).all()) and bool((s[:, 1] < s[:, 2]).all())
-    key = s[:, 0] * N * N + s[:, 1] * N + s[:, 2]
-    assert torch.unique(key).numel() == s.shape[0]
+    assert torch.unique(s, dim=0).shape[0] == s.shape[0]
     a, b = edges[:, 0].to(torch.int64), edges[:, 1].to(torch.int64)
     del edges
     keys = torch.minimum(a, b) * N + torch.maximum(a, b)
