@@ -165,18 +165,81 @@ __device__ __forceinline__ bool bucket_find(const uint32_t *H, int lgb, uint32_t
 // Filter bit of rank r (2^20 bits) for the hub tier's shared-memory filter.
 __device__ __forceinline__ uint32_t fslot(uint32_t r) { return (r * 0x85EBCA77u) >> 12; }
 
-// Lookup in a hash table in global memory that this CTA filled with atomics
-// at the L2: read past the L1, which may hold lines of an earlier task's table.
-__device__ __forceinline__ bool hash_find_global(const uint32_t *H, int lg, uint32_t z) {
-  const uint32_t mask = (1u << lg) - 1u;
-  uint32_t h = hslot(z, lg);
-  for (;;) {
-    const uint32_t v = __ldcg(H + h);
-    if (v == z) return true;
-    if (v == kEmpty) return false;
-    h = (h + 1) & mask;
+// Membership tests of the walk: one(z) for a single key, check4 for the four
+// keys of a lane's 16-byte load, with the four first probes issued before any
+// result is used (the rare longer searches follow one by one).
+struct WarpHashMember {  // linear probing, per-warp table of 2^lg slots
+  const uint32_t *H;
+  int lg;
+  __device__ bool one(uint32_t z) const { return hash_find(H, lg, z); }
+  __device__ void check4(const uint32_t z[4], bool r[4]) const {
+    uint32_t h[4], v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      h[u] = hslot(z[u], lg);
+      v[u] = H[h[u]];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      r[u] = v[u] == z[u];
+      if (!r[u] && v[u] != kEmpty) r[u] = hash_find(H, lg, z[u]);
+    }
   }
-}
+};
+
+struct BucketMember {  // four-slot buckets, 2^lgb buckets
+  const uint32_t *H;
+  int lgb;
+  __device__ bool one(uint32_t z) const { return bucket_find(H, lgb, z); }
+  __device__ void check4(const uint32_t z[4], bool r[4]) const {
+    uint4 q[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) q[u] = reinterpret_cast<const uint4 *>(H)[bslot(z[u], lgb)];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      r[u] = q[u].x == z[u] || q[u].y == z[u] || q[u].z == z[u] || q[u].w == z[u];
+      if (!r[u] && q[u].w != kEmpty) r[u] = bucket_find(H, lgb, z[u]);
+    }
+  }
+};
+
+struct BitmapMember {  // one bit per rank (the boolean array B, bit-packed)
+  const uint32_t *B;
+  __device__ bool one(uint32_t z) const { return ((B[z >> 5] >> (z & 31)) & 1u) != 0; }
+  __device__ void check4(const uint32_t z[4], bool r[4]) const {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) r[u] = one(z[u]);
+  }
+};
+
+struct FilterMember {  // one bit per hashed rank: may answer yes wrongly
+  const uint32_t *F;
+  __device__ bool one(uint32_t z) const {
+    const uint32_t f = fslot(z);
+    return ((F[f >> 5] >> (f & 31)) & 1u) != 0;
+  }
+  __device__ void check4(const uint32_t z[4], bool r[4]) const {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) r[u] = one(z[u]);
+  }
+};
+
+struct SortedRowMember {  // binary search in the sorted probe list
+  const uint32_t *P;
+  uint64_t n;
+  __device__ bool one(uint32_t z) const {
+    uint64_t lo = 0, hi = n;
+    while (lo < hi) {
+      const uint64_t mid = (lo + hi) >> 1;
+      if (P[mid] < z) lo = mid + 1; else hi = mid;
+    }
+    return lo < n && P[lo] == z;
+  }
+  __device__ void check4(const uint32_t z[4], bool r[4]) const {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) r[u] = one(z[u]);
+  }
+};
 
 // Task fetch shared by all kernels: returns the task id or -1.  Thread 0
 // only; the caller broadcasts.
@@ -232,11 +295,92 @@ struct WarpOut {
   bool failed;                     // a reservation did not fit: the warp stopped
 };
 
+// Exact-membership checks applied to a warp's staged entries before they are
+// written.  NoVerify: the walk's test was exact already.  GlobalHashVerify:
+// the walk tested a shared-memory filter only; the CTA's hash table in global
+// memory decides, four keys per lane in flight.
+struct NoVerify {
+  static constexpr bool kActive = false;
+  __device__ void check4(const uint32_t *, const bool *, bool *) const {}
+};
+
+struct GlobalHashVerify {
+  static constexpr bool kActive = true;
+  const uint32_t *H;
+  int lg;
+  __device__ void check4(const uint32_t z[4], const bool valid[4], bool res[4]) const {
+    const uint32_t mask = (1u << lg) - 1u;
+    uint32_t h[4];
+    bool open[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      h[u] = hslot(z[u], lg);
+      res[u] = false;
+      open[u] = valid[u];
+    }
+    for (;;) {  // linear probing; the four searches advance together
+      uint32_t v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = open[u] ? __ldcg(H + h[u]) : 0u;
+      bool more = false;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (!open[u]) continue;
+        if (v[u] == z[u]) {
+          res[u] = true;
+          open[u] = false;
+        } else if (v[u] == kEmpty) {
+          open[u] = false;
+        } else {
+          h[u] = (h[u] + 1) & mask;
+          more = true;
+        }
+      }
+      if (!more) break;
+    }
+  }
+};
+
+// Keep the staged entries (original id of y, rank of z) whose z passes the
+// exact check, compacted in place; returns how many are left.
+template <class Verify>
+__device__ __forceinline__ uint32_t warp_verify(uint32_t *buf, uint32_t cnt, const Verify &vf) {
+  if (!Verify::kActive) return cnt;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  uint2 *b2 = reinterpret_cast<uint2 *>(buf);
+  uint32_t out = 0;
+  for (uint32_t i0 = 0; i0 < cnt; i0 += 128) {
+    uint2 e[4];
+    uint32_t z[4];
+    bool valid[4], keep[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const uint32_t i = i0 + 32 * u + lane;
+      valid[u] = i < cnt;
+      e[u] = valid[u] ? b2[i] : make_uint2(0, 0);
+      z[u] = e[u].y;
+    }
+    vf.check4(z, valid, keep);
+    __syncwarp();  // every entry of this round is read before any is moved
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const unsigned km = __ballot_sync(0xffffffffu, keep[u]);
+      if (keep[u]) b2[out + __popc(km & lt)] = e[u];
+      out += __popc(km);
+    }
+    __syncwarp();
+  }
+  return out;
+}
+
 // Copy a warp's buffer of cnt > 0 entries (original id of y, rank of z) to
 // the chunk as sorted original-id triples with x, after reserving room with
-// one atomic; four gathers of z per lane are issued together.  Returns false
-// if the chunk is full.  Scalar arguments only, so that the caller's state
-// stays in registers around the call.
+// one atomic.  The triples are written with 16-byte streaming stores, four
+// triples (three uint4) per lane, after a head of at most three single
+// triples that brings the destination to a 16-byte boundary; each lane's
+// four z gathers are issued together.  Returns false if the chunk is full.
+// Scalar arguments only, so that the caller's state stays in registers.
 __device__ __noinline__ bool warp_flush(ListCtl *ctl, uint32_t *chunk, uint64_t chunk_cap,
                                         const uint32_t *__restrict__ inv, const uint32_t *buf,
                                         uint32_t cnt, uint32_t inv_x) {
@@ -258,25 +402,42 @@ __device__ __noinline__ bool warp_flush(ListCtl *ctl, uint32_t *chunk, uint64_t 
   pos = (unsigned long long)__shfl_sync(0xffffffffu, (long long)pos, 0);
   uint32_t *dst = chunk + 3ull * pos;
   const uint2 *b2 = reinterpret_cast<const uint2 *>(buf);
-  for (uint32_t i0 = lane; i0 < cnt; i0 += 128) {
+  // dst sits `mis` words past a 16-byte boundary; triple i starts 3 i words
+  // later, on a boundary when mis + 3 i = 0 mod 4, i.e. for i = mis mod 4
+  const uint32_t mis = (uint32_t)((reinterpret_cast<uintptr_t>(dst) >> 2) & 3u);
+  const uint32_t head = mis < cnt ? mis : cnt;
+  const uint32_t groups = (cnt - head) >> 2;
+  const uint32_t tail0 = head + 4 * groups;
+  // head and tail (at most three triples each): one triple per lane
+  auto one = [&](uint32_t i) {
+    const uint2 e = b2[i];
+    uint32_t p = inv_x, q = e.x, r = __ldg(inv + e.y);
+    sort3(p, q, r);
+    __stcs(dst + 3 * i, p);
+    __stcs(dst + 3 * i + 1, q);
+    __stcs(dst + 3 * i + 2, r);
+  };
+  if ((uint32_t)lane < head) one(lane);
+  if ((uint32_t)lane < cnt - tail0) one(tail0 + lane);
+  // body: four consecutive triples per lane, three aligned 16-byte stores
+  uint4 *d4 = reinterpret_cast<uint4 *>(dst + 3 * head);
+  for (uint32_t gi = lane; gi < groups; gi += 32) {
+    const uint32_t i = head + 4 * gi;
     uint2 e[4];
+    uint32_t t[4][3];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (i0 + 32 * u < cnt) e[u] = b2[i0 + 32 * u];
+    for (int u = 0; u < 4; ++u) e[u] = b2[i + u];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (i0 + 32 * u < cnt) e[u].y = __ldg(inv + e[u].y);
+    for (int u = 0; u < 4; ++u) t[u][2] = __ldg(inv + e[u].y);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const uint32_t i = i0 + 32 * u;
-      if (i < cnt) {
-        uint32_t p = inv_x, q = e[u].x, r = e[u].y;
-        sort3(p, q, r);
-        __stcs(dst + 3 * i, p);
-        __stcs(dst + 3 * i + 1, q);
-        __stcs(dst + 3 * i + 2, r);
-      }
+      t[u][0] = inv_x;
+      t[u][1] = e[u].x;
+      sort3(t[u][0], t[u][1], t[u][2]);
     }
+    __stcs(d4 + 3 * gi, make_uint4(t[0][0], t[0][1], t[0][2], t[1][0]));
+    __stcs(d4 + 3 * gi + 1, make_uint4(t[1][1], t[1][2], t[2][0], t[2][1]));
+    __stcs(d4 + 3 * gi + 2, make_uint4(t[2][2], t[3][0], t[3][1], t[3][2]));
   }
   __syncwarp();
   return true;
@@ -284,8 +445,11 @@ __device__ __noinline__ bool warp_flush(ListCtl *ctl, uint32_t *chunk, uint64_t 
 
 // Commit a warp's buffer: afterwards every test before `cur` is committed.
 // On a full chunk sets o.failed and leaves o.safe where it was.
+template <class Verify>
 __device__ __forceinline__ bool warp_commit(const ListArgs &a, WarpOut &o, uint32_t inv_x,
-                                            uint64_t cur, unsigned long long probes) {
+                                            uint64_t cur, unsigned long long probes,
+                                            const Verify &vf) {
+  if (o.cnt > 0) o.cnt = warp_verify(o.buf, o.cnt, vf);
   if (o.cnt > 0) {
     if (!warp_flush(a.ctl, a.chunk, a.chunk_cap, a.inv, o.buf, o.cnt, inv_x)) {
       o.failed = true;
@@ -357,17 +521,19 @@ __device__ void commit_warp(ListCtl *ctl, const ListArgs &a, int64_t t, const ui
 
 // Warp-level walk of the tests [i0, i1) of B vertex x, whose seed row is
 // [pb, pe) (entries of sadj); k0 is the seed edge holding test i0 (found by
-// binary search when ~0).  For each test: z = the scanned element, member(z) = B[z].  Hits
+// binary search when ~0).  For each test: z = the scanned element, and
+// member (one key, or four at a time) answers B[z].  Hits
 // go to the warp's own global slab as (original id of x, original id of y,
 // rank of z) at positions counted by wcnt (kEmit 0, warp tiers), or to the
 // warp's shared-memory buffer as (original id of y, rank of z), flushed to the
 // chunk whenever it could overflow in the next step (kEmit 1, CTA tiers: on a
 // failed flush the walk stops with o.failed set).
-template <int kEmit, class Member>
+template <int kEmit, bool kPrefetch, class Member, class Verify = NoVerify>
 __device__ __forceinline__ void scan_items(const ListArgs &a, uint64_t pb, uint64_t pe, uint64_t k0,
                                            uint64_t i0, uint64_t i1, uint32_t inv_x,
                                            Member member, uint32_t *slab, WarpOut &o,
-                                           uint32_t &wcnt, unsigned long long &probes) {
+                                           uint32_t &wcnt, unsigned long long &probes,
+                                           const Verify &vf = Verify()) {
   if (i0 >= i1) return;
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
@@ -440,20 +606,33 @@ __device__ __forceinline__ void scan_items(const ListArgs &a, uint64_t pb, uint6
       // lead <= e < lead + run.
       const uint32_t *src = a.scan_adj + (Aj & ~3ull);
       const uint32_t lead = (uint32_t)(Aj & 3), span = lead + run;
+      // With kPrefetch (kernels with registers to spare) the next iteration's
+      // 16 bytes are loaded one iteration ahead.  Only a run's first and last
+      // iterations hold elements outside the run; their tests are masked, and
+      // probes are counted once per run.
+      uint4 vn = make_uint4(0, 0, 0, 0);
+      if (kPrefetch && 4u * lane < span) vn = *reinterpret_cast<const uint4 *>(src + 4 * lane);
       for (uint32_t e0 = 0; e0 < span; e0 += 128) {
         if (kEmit == 1 && o.cnt > kWarpBuf - kWarpStep) {
           // every test before this iteration's first one has its hits in buf
-          // (and is counted in lane 0's probes)
-          if (!warp_commit(a, o, inv_x, base + (e0 > lead ? e0 - lead : 0), probes)) return;
+          const uint32_t done = e0 > lead ? e0 - lead : 0;
+          if (!warp_commit(a, o, inv_x, base + done, probes + (lane == 0 ? done : 0), vf))
+            return;
         }
         const uint32_t e = e0 + 4 * lane;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (e < span) v = *reinterpret_cast<const uint4 *>(src + e);
+        uint4 v = vn;
+        if (kPrefetch) {
+          if (e + 128 < span) vn = *reinterpret_cast<const uint4 *>(src + e + 128);
+        } else if (e < span) {
+          v = *reinterpret_cast<const uint4 *>(src + e);
+        }
         const uint32_t z[4] = {v.x, v.y, v.z, v.w};
-        if (lane == 0) probes += (e0 + 128 < span ? e0 + 128 : span) - (e0 > lead ? e0 : lead);
         bool hit[4];
+        member.check4(z, hit);
+        if (e0 < lead || e0 + 128 > span) {  // the same for the whole warp
 #pragma unroll
-        for (int u = 0; u < 4; ++u) hit[u] = e + u - lead < run && member(z[u]);
+          for (int u = 0; u < 4; ++u) hit[u] = hit[u] && e + u - lead < run;
+        }
         // positions: the hits of element u of all lanes, u = 0..3, one after
         // the other (the order of triangles is free)
         unsigned hm[4];
@@ -487,12 +666,13 @@ __device__ __forceinline__ void scan_items(const ListArgs &a, uint64_t pb, uint6
           }
         }
       }
+      if (lane == 0) probes += run;
       base += run;
       continue;
     }
     // Short segments: one step of up to 32 tests spread over several lists.
     if (kEmit == 1 && o.cnt > kWarpBuf - kWarpStep) {
-      if (!warp_commit(a, o, inv_x, base, probes)) return;
+      if (!warp_commit(a, o, inv_x, base, probes, vf)) return;
     }
     uint64_t lim = base + 32;
     if (lim > i1) lim = i1;
@@ -510,7 +690,7 @@ __device__ __forceinline__ void scan_items(const ListArgs &a, uint64_t pb, uint6
     if (act) {
       z = a.scan_adj[Aj + base + off];
       ++probes;
-      hit = member(z);
+      hit = member.one(z);
     }
     emit(hit, iyj, z);
     base = lim;
@@ -547,8 +727,8 @@ __global__ void __launch_bounds__(kWarpThreads, 4) k_list_warp(ListArgs a) {
       __syncwarp();
       for (uint64_t q = pb + lane; q < pe; q += 32) hash_insert(H, lg, a.padj[q]);
       __syncwarp();
-      scan_items<0>(a, sb, se, sb, a.WP[sb], a.WP[se], a.inv[x],
-                    [&](uint32_t z) { return hash_find(H, lg, z); }, slab, nout, cnt, probes);
+      scan_items<0, false>(a, sb, se, sb, a.WP[sb], a.WP[se], a.inv[x], WarpHashMember{H, lg},
+                           slab, nout, cnt, probes);
       __syncwarp();
     }
 #pragma unroll
@@ -645,8 +825,11 @@ __global__ void __launch_bounds__(THREADS, TIER == kTierLarge ? 1 : (TIER == kTi
     const uint32_t mode = s_mode;
     const int lg = (int)s_lg;
     const uint64_t wa = s_rng[wid][0], wb = s_rng[wid][1];  // this warp's tests
-    // build B: the probe set P_x
-    if (mode == 0) {
+    // build B: the probe set P_x (narrow and mid vertices always take mode
+    // 1, so the other modes are compiled for the large kernel only)
+    constexpr bool kLarge = TIER == kTierLarge;
+    constexpr bool kPf = TIER == kTierNarrow;  // registers allow the walk's prefetch
+    if (kLarge && mode == 0) {
       for (uint64_t q = pb + threadIdx.x; q < pe; q += THREADS) {
         const uint32_t r = a.padj[q];
         atomicOr(&sm[r >> 5], 1u << (r & 31));
@@ -656,7 +839,7 @@ __global__ void __launch_bounds__(THREADS, TIER == kTierLarge ? 1 : (TIER == kTi
       __syncthreads();
       for (uint64_t q = pb + threadIdx.x; q < pe; q += THREADS)
         bucket_insert(sm, lg - 2, a.padj[q]);
-    } else if (mode == 3) {
+    } else if (kLarge && mode == 3) {
       uint32_t *gh = a.ghash + (uint64_t)blockIdx.x * kGHashSlots;
       for (uint32_t i = threadIdx.x; i < kFilterWords; i += THREADS) sm[i] = 0;
       for (uint32_t i = threadIdx.x; i < (1u << lg); i += THREADS) gh[i] = kEmpty;
@@ -675,36 +858,24 @@ __global__ void __launch_bounds__(THREADS, TIER == kTierLarge ? 1 : (TIER == kTi
     o.safe = wa;
     o.probes_safe = 0;
     o.failed = false;
-    if (mode == 0) {
-      scan_items<1>(a, sb, se, ~0ull, wa, wb, inv_x,
-                    [&](uint32_t z) { return ((sm[z >> 5] >> (z & 31)) & 1u) != 0; }, nullptr,
-                    o, unused, probes);
-    } else if (mode == 1) {
-      scan_items<1>(a, sb, se, ~0ull, wa, wb, inv_x,
-                    [&](uint32_t z) { return bucket_find(sm, lg - 2, z); }, nullptr, o, unused,
-                    probes);
+    if (kLarge && mode == 0) {
+      scan_items<1, kPf>(a, sb, se, ~0ull, wa, wb, inv_x, BitmapMember{sm}, nullptr, o, unused,
+                         probes);
+    } else if (!kLarge || mode == 1) {
+      scan_items<1, kPf>(a, sb, se, ~0ull, wa, wb, inv_x, BucketMember{sm, lg - 2}, nullptr, o,
+                         unused, probes);
     } else if (mode == 3) {
-      const uint32_t *gh = a.ghash + (uint64_t)blockIdx.x * kGHashSlots;
-      scan_items<1>(a, sb, se, ~0ull, wa, wb, inv_x,
-                    [&](uint32_t z) {
-                      const uint32_t f = fslot(z);
-                      if (((sm[f >> 5] >> (f & 31)) & 1u) == 0) return false;
-                      return hash_find_global(gh, lg, z);
-                    },
-                    nullptr, o, unused, probes);
+      // the walk tests the shared filter only; the staged candidates are
+      // checked against the CTA's global hash table when the warp flushes
+      const GlobalHashVerify vf{a.ghash + (uint64_t)blockIdx.x * kGHashSlots, lg};
+      scan_items<1, kPf>(a, sb, se, ~0ull, wa, wb, inv_x, FilterMember{sm}, nullptr, o, unused,
+                         probes, vf);
+      if (!o.failed) warp_commit(a, o, inv_x, wb, probes, vf);
     } else {
-      scan_items<1>(a, sb, se, ~0ull, wa, wb, inv_x,
-                    [&](uint32_t z) {
-                      uint64_t lo = pb, hi = pe;
-                      while (lo < hi) {
-                        const uint64_t mid = (lo + hi) >> 1;
-                        if (a.padj[mid] < z) lo = mid + 1; else hi = mid;
-                      }
-                      return lo < pe && a.padj[lo] == z;
-                    },
-                    nullptr, o, unused, probes);
+      scan_items<1, kPf>(a, sb, se, ~0ull, wa, wb, inv_x,
+                         SortedRowMember{a.padj + pb, pe - pb}, nullptr, o, unused, probes);
     }
-    if (!o.failed) warp_commit(a, o, inv_x, wb, probes);
+    if (!o.failed && (!kLarge || mode != 3)) warp_commit(a, o, inv_x, wb, probes, NoVerify());
     // commit the warp's tests before o.safe; queue the rest for the next launch
     unsigned long long done = o.probes_safe;
 #pragma unroll
@@ -735,7 +906,7 @@ __global__ void __launch_bounds__(THREADS, TIER == kTierLarge ? 1 : (TIER == kTi
         s_nfail = 0;
       }
     }
-    if (mode == 0) {  // reset B
+    if (kLarge && mode == 0) {  // reset B
       for (uint64_t q = pb + threadIdx.x; q < pe; q += THREADS) sm[a.padj[q] >> 5] = 0;
     }
   }
