@@ -328,10 +328,12 @@ def run_listing(args, key: str, steps: int, warmup: int, e2e: bool, orderings: b
     import torch
 
     import paper_2203_04774_gb300 as tl
+    from paper_2203_04774_gb300 import autotune
     from paper_2203_04774_gb300.synth import device as sdev
 
     world, rank, local = dist_setup()
     wl = WORKLOADS[key]
+    table = autotune.load_table()
     t0 = time.time()
     e_host = r_host = None
     if wl["generator"] == "Chung-Lu":
@@ -380,6 +382,9 @@ def run_listing(args, key: str, steps: int, warmup: int, e2e: bool, orderings: b
             costs = [tl.tl_cost(g, a) for a in (tl.TL_APP, tl.TL_APM)]
             out = []
             for i, a in enumerate((tl.TL_APP, tl.TL_APM)):
+                # the work split picked by the autotuner for this listing's
+                # work profile (a profile kernel and a table lookup, timed)
+                autotune.apply(g, a, table)
                 ch.reset()
                 nt = tl.tl_list_triangles(g, a, CHUNK_BYTES, ch_ptr, ch.user)
                 phase_ev[3 + i].record(stream)
@@ -485,6 +490,7 @@ def run_listing(args, key: str, steps: int, warmup: int, e2e: bool, orderings: b
                      "compulsory_bytes_per_step": len(costs) * (8 * m + 12 * T),
                      "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"},
         "list_stats": {a: r[3] for a, r in zip(("A++", "A+-"), out)},
+        "work_split": "autotuned per work profile (paper_2203_04774_gb300/tuning_table.json)",
         "phase_ms_median": timed_phase_ms,
         "gpu_launches": launches,
         "clocks": clk,
@@ -548,11 +554,16 @@ def run_batch(args, steps: int, warmup: int) -> dict:
     vb = np.zeros(k + 1, np.int64)
     np.cumsum(ns, out=vb[1:])
 
-    def batched():
+    from paper_2203_04774_gb300 import autotune
+    table = autotune.load_table()
+
+    def batched(tuned=True):
         u = tl.tl_graph_load_parts(ns, pairs, e_all, stream.cuda_stream)
         try:
             tl.tl_order_compute(u, tl.TL_ORDER_DEGREE, rank_all)
             tl.tl_order_apply(u, rank_all)
+            if tuned:  # the autotuner's split for the union's work profile
+                autotune.apply(u, tl.TL_APP, table)
             chp.reset()
             nt = tl.tl_list_triangles(u, tl.TL_APP, CHUNK_BYTES, chp.fn(), chp.user)
             m = tl.tl_graph_size(u)[1]
@@ -583,13 +594,13 @@ def run_batch(args, steps: int, warmup: int) -> dict:
             lat[i] = time.perf_counter() - t1
         return int(c.sum()), m, c, h, lat
 
-    def timed(fn, reps):
+    def timed(fn, reps, *fa):
         out, ms = None, []
         for _ in range(reps):
             flush.zero_()
             torch.cuda.synchronize()
             t1 = time.perf_counter()
-            out = fn()
+            out = fn(*fa)
             torch.cuda.synchronize()
             ms.append((time.perf_counter() - t1) * 1e3)
         return out, ms
@@ -601,6 +612,8 @@ def run_batch(args, steps: int, warmup: int) -> dict:
     launches0 = tl.tl_kernel_launches()
     (nt, m, cb, hb, st), b_ms = timed(batched, steps)
     b_launches = (tl.tl_kernel_launches() - launches0) / steps
+    batched(False)
+    (nt2, m2, cb2, hb2, st2), f_ms = timed(batched, steps, False)
     per_warm = 1
     for _ in range(per_warm):
         per_graph()
@@ -610,10 +623,12 @@ def run_batch(args, steps: int, warmup: int) -> dict:
     clk = clocks.stop()
     assert nt == nt1 and m == m1, (nt, nt1, m, m1)
     assert np.array_equal(cb, c1) and np.array_equal(hb, h1), "per-graph results differ"
-    # oracle spot check on the smallest graphs
+    assert np.array_equal(cb, cb2) and np.array_equal(hb, hb2), "the work split changed results"
+    # oracle spot check on the three smallest and three other graphs
     import oracle
     spot = []
-    for i in np.argsort(ns)[:3]:
+    others = np.random.default_rng(3).choice(k, 3, replace=False)
+    for i in list(np.argsort(ns)[:3]) + list(others):
         e = e_all[po[i]:po[i + 1]].cpu().numpy().view(np.uint32)
         g = oracle.Graph(int(ns[i]), e)
         r = rank_all[vb[i]:vb[i + 1]].cpu().numpy().view(np.uint32)
@@ -622,6 +637,7 @@ def run_batch(args, steps: int, warmup: int) -> dict:
         spot.append(bool(rc == int(cb[i]) and rh == int(hb[i])))
     assert all(spot), spot
     b_s = statistics.median(b_ms) / 1e3
+    f_s = statistics.median(f_ms) / 1e3
     p_s = statistics.median(p_ms) / 1e3
     line = {
         "metric": "graphs/s (batched disjoint-union pass vs one pass per graph)",
@@ -635,7 +651,12 @@ def run_batch(args, steps: int, warmup: int) -> dict:
                     "edges_per_s": m / b_s, "gpu_launches_per_step": b_launches,
                     "latency_s": {"p50": b_s, "p99": b_s,
                                   "note": "every graph completes when the pass ends"},
-                    "list_kernel_ms": sum(st["kernel_ms"]), "list_stats": st},
+                    "list_kernel_ms": sum(st["kernel_ms"]), "list_stats": st,
+                    "work_split": "autotuned for the union's work profile"},
+        "batched_fixed_split": {"s_per_step": f_s, "graphs_per_s": k / f_s,
+                                "list_kernel_ms": sum(st2["kernel_ms"]),
+                                "work_split": "library defaults"},
+        "autotune_gain": f_s / b_s,
         "per_graph": {"s_per_step": p_s, "graphs_per_s": k / p_s, "triangles_per_s": nt / p_s,
                       "edges_per_s": m / p_s, "gpu_launches_per_step": p_launches,
                       "latency_s": {"p50": float(np.percentile(lat, 50)),

@@ -205,21 +205,26 @@ TL_EXPORT tl_status tl_list_triangles_range(tl_graph *g, tl_alg alg, uint32_t x_
 
 /* The work split of the listing kernels: how the outer loop of Algorithms 1
  * and 2 (Sec. 2.1; for each vertex x, the seeds of x, each with its scanned
- * list) is cut into device tasks.  The paper runs that loop on one thread;
+ * list) is cut into device tasks, and which kernel (which membership
+ * structure for B) takes each vertex.  The paper runs that loop on one thread;
  * these are choices of the GPU path that change speed only, never the
  * triangles, their count or the probe count.  Each "B vertex" x (w for A++,
  * u for A+-, v for A--) with probe-set size p (the list marked in B) and W
- * membership tests goes to one of five kernels:
- *   small   p <= 32,   W <= warp_work: one warp, vertices grouped per task
- *   medium  p <= 1024, W <= warp_work: one warp, vertices grouped per task
- *   narrow  p <= 256,  W >  warp_work: one-warp CTAs, pieces of narrow_piece tests
- *   mid     p <= 2048, W >  warp_work: 256-thread CTAs, pieces of mid_piece tests
- *   large   p >  2048:                 1024-thread CTAs, pieces of
+ * membership tests goes to the first of five kernels that takes it:
+ *   small   p <= small_max_p,  W <= warp_work: one warp, vertices grouped per task
+ *   medium  p <= medium_max_p, W <= warp_work: one warp, vertices grouped per task
+ *   narrow  p <= narrow_max_p: one-warp CTAs, pieces of narrow_piece tests
+ *   mid     p <= mid_max_p:    256-thread CTAs, pieces of mid_piece tests
+ *   large   any p:             1024-thread CTAs, pieces of
  *           clamp(large_per_p * p, large_min, large_max) tests (large_max is
  *           further capped at 1/16 of the listing's work per large CTA)
  * Every piece rebuilds B, so larger pieces amortise that build; smaller ones
  * balance the end of a launch. */
 typedef struct {
+  uint32_t small_max_p;  /* <= 32   (per-warp table of 64 slots) */
+  uint32_t medium_max_p; /* <= 1024 (per-warp table of 2048 slots) */
+  uint32_t narrow_max_p; /* <= 256  (per-CTA table of 1024 slots) */
+  uint32_t mid_max_p;    /* <= 2048 (per-CTA table of 8192 slots) */
   uint32_t warp_work;    /* 256 .. 4096 */
   uint32_t narrow_piece; /* >= 1024 */
   uint32_t mid_piece;    /* >= 1024 */
@@ -233,6 +238,21 @@ TL_EXPORT tl_status tl_default_tuning(tl_tuning *out);
  * A value outside the ranges above -> TL_EINVAL, and g keeps its split. */
 TL_EXPORT tl_status tl_set_tuning(tl_graph *g, const tl_tuning *t);
 TL_EXPORT tl_status tl_get_tuning(const tl_graph *g, tl_tuning *out);
+
+/* The work profile of a listing, the degree profile the work split is
+ * chosen by (see paper_2203_04774_gb300/autotune.py): for the B vertices x
+ * of rank [x_begin, x_end) (w for A++, u for A+-, v for A--), with probe-set
+ * size p_x and W_x membership tests (so that the W_x add up to the cost of
+ * Sec. 3.1 over the range, by Property 1),
+ *   hist[bp * TL_PROFILE_BINS_W + bw] = sum of W_x over the x with
+ *   bit_length(p_x) = bp and bit_length(W_x) = bw
+ * (bit_length(0) = 0; larger values fall in the last bin).  hist is a host
+ * array of TL_PROFILE_BINS_P * TL_PROFILE_BINS_W uint64, filled in full.
+ * The paper has no counterpart. */
+#define TL_PROFILE_BINS_P 33
+#define TL_PROFILE_BINS_W 48
+TL_EXPORT tl_status tl_work_profile(tl_graph *g, tl_alg alg, uint32_t x_begin, uint32_t x_end,
+                                    uint64_t *hist);
 
 /* A ready-made consumer: count the triples and add up their set hash
  *   H = sum over triples of h(a,b,c)  (mod 2^64),

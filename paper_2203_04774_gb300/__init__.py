@@ -69,7 +69,9 @@ class ListStats(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     """tl_tuning: the work split of the listing kernels (speed only)."""
-    _fields_ = [("warp_work", _U32), ("narrow_piece", _U32), ("mid_piece", _U32),
+    _fields_ = [("small_max_p", _U32), ("medium_max_p", _U32), ("narrow_max_p", _U32),
+                ("mid_max_p", _U32), ("warp_work", _U32), ("narrow_piece", _U32),
+                ("mid_piece", _U32),
                 ("large_per_p", _U32), ("large_min", _U32), ("large_max", _U32)]
 
     def as_dict(self) -> dict:
@@ -91,6 +93,7 @@ SIGNATURES = {
     "tl_count_hash_release": ([ctypes.POINTER(CountHashState)], None),
     "tl_graph_csr": ([_P, _I, _P, _P], _I),
     "tl_default_tuning": ([ctypes.POINTER(Tuning)], _I),
+    "tl_work_profile": ([_P, _I, _U32, _U32, _P], _I),
     "tl_set_tuning": ([_P, ctypes.POINTER(Tuning)], _I),
     "tl_get_tuning": ([_P, ctypes.POINTER(Tuning)], _I),
     "tl_server_create": ([ctypes.POINTER(_P), ctypes.POINTER(ServerConfig)], _I),
@@ -304,6 +307,19 @@ def tl_last_list_stats(g) -> dict:
             "kernel_triangles": [int(v) for v in st.kernel_triangles],
             "bucketize_ms": float(st.bucketize_ms), "consumer_ms": float(st.consumer_ms),
             "wall_ms": float(st.wall_ms)}
+
+
+TL_PROFILE_BINS_P, TL_PROFILE_BINS_W = 33, 48
+
+
+def tl_work_profile(g, alg: int, x_begin: int = 0, x_end: int | None = None) -> np.ndarray:
+    """uint64 [TL_PROFILE_BINS_P, TL_PROFILE_BINS_W]: summed tests W_x of the
+    B vertices by bit length of their probe-set size p_x and of W_x."""
+    if x_end is None:
+        x_end = tl_graph_size(g)[0]
+    h = np.zeros(TL_PROFILE_BINS_P * TL_PROFILE_BINS_W, dtype=np.uint64)
+    _check(lib().tl_work_profile(g, alg, x_begin, x_end, h.ctypes.data), "tl_work_profile")
+    return h.reshape(TL_PROFILE_BINS_P, TL_PROFILE_BINS_W)
 
 
 def tl_default_tuning() -> dict:

@@ -64,6 +64,10 @@ struct PinnedCtl {
 namespace {
 tl_tuning tl_default_tuning_value() {
   tl_tuning t;
+  t.small_max_p = tl::kSmallMaxP;
+  t.medium_max_p = tl::kMediumMaxP;
+  t.narrow_max_p = tl::kNarrowMaxP;
+  t.mid_max_p = tl::kMidMaxP;
   t.warp_work = (uint32_t)tl::kWarpWorkMax;
   t.narrow_piece = 1u << 14;
   t.mid_piece = 1u << 16;
@@ -87,6 +91,7 @@ struct tl_graph {
   cudaEvent_t ev[2] = {nullptr, nullptr};
   tl_list_stats stats{};
   int cached_alg = -1;
+  int wp_alg = -1;  // the algorithm WP was computed for (-1: none)
   uint32_t cached_xb = 0, cached_xe = 0;
   uint64_t n_tasks[tl::kTiers] = {0, 0, 0, 0, 0};
   // the work split: as set by tl_set_tuning, and as used by the cached tables
@@ -135,6 +140,7 @@ namespace {
 void ensure_ordered(tl_graph *G) {
   if (!G->g.ordered) {
     G->cached_alg = -1;
+    G->wp_alg = -1;
     tl::build_dag(G->g, nullptr, true);
   }
 }
@@ -177,6 +183,10 @@ T read_dev(const T *p, cudaStream_t s) {
 // so that no single piece holds up the end of the launch on a small graph.
 tl::Tuning effective_tuning(const tl_tuning &t, uint64_t range_work) {
   tl::Tuning tu;
+  tu.small_max_p = t.small_max_p;
+  tu.medium_max_p = t.medium_max_p;
+  tu.narrow_max_p = t.narrow_max_p;
+  tu.mid_max_p = t.mid_max_p;
   tu.warp_work = t.warp_work;
   tu.narrow_piece = t.narrow_piece;
   tu.mid_piece = t.mid_piece;
@@ -189,27 +199,39 @@ tl::Tuning effective_tuning(const tl_tuning &t, uint64_t range_work) {
 }
 
 bool same_tuning(const tl::Tuning &a, const tl::Tuning &b) {
-  return a.warp_work == b.warp_work && a.narrow_piece == b.narrow_piece &&
+  return a.small_max_p == b.small_max_p && a.medium_max_p == b.medium_max_p &&
+         a.narrow_max_p == b.narrow_max_p && a.mid_max_p == b.mid_max_p &&
+         a.warp_work == b.warp_work && a.narrow_piece == b.narrow_piece &&
          a.mid_piece == b.mid_piece && a.large_per_p == b.large_per_p &&
          a.large_min == b.large_min && a.large_max == b.large_max;
+}
+
+// WP, the exclusive prefix of the scanned-list lengths over all seed-side
+// entries of one algorithm (the flat work space; kept until the DAG changes).
+void ensure_wp(tl_graph *G, int alg) {
+  if (G->wp_alg == alg) return;
+  tl::DeviceGraph &g = G->g;
+  cudaStream_t s = g.stream;
+  const uint64_t m = g.m;
+  const Sides sd = sides(g, alg);
+  G->wseed.reserve((m ? m : 1) * 4);
+  G->WP.reserve((m + 1) * 8);
+  if (m) tl::launch_seed_work(sd.sadj, m, sd.scan_off, G->wseed.as<uint32_t>(), s);
+  tl::exclusive_scan_u32_to_u64(G->wseed.as<uint32_t>(), G->WP.as<uint64_t>(), m, g.scan_tmp, s);
+  G->wp_alg = alg;
+  G->cached_alg = -1;  // task tables of another algorithm used the old WP
 }
 
 // a6: per-seed-edge work prefix and the task counts of every kernel.
 void bucketize(tl_graph *G, int alg, uint32_t xb, uint32_t xe) {
   tl::DeviceGraph &g = G->g;
   cudaStream_t s = g.stream;
-  const uint64_t m = g.m;
   const Sides sd = sides(g, alg);
-  if (!(G->cached_alg == alg && G->cached_xb == xb && G->cached_xe == xe)) {
-    G->wseed.reserve((m ? m : 1) * 4);
-    G->WP.reserve((m + 1) * 8);
-    if (m) tl::launch_seed_work(sd.sadj, m, sd.scan_off, G->wseed.as<uint32_t>(), s);
-    tl::exclusive_scan_u32_to_u64(G->wseed.as<uint32_t>(), G->WP.as<uint64_t>(), m, g.scan_tmp,
-                                  s);
-  }
-  const uint64_t kb = read_dev(sd.soff + xb, s), ke = read_dev(sd.soff + xe, s);
-  const uint64_t range_work =
-      read_dev(G->WP.as<uint64_t>() + ke, s) - read_dev(G->WP.as<uint64_t>() + kb, s);
+  ensure_wp(G, alg);
+  G->ctl.reserve(sizeof(tl::ListCtl));
+  uint64_t *rw = reinterpret_cast<uint64_t *>(G->ctl.p);  // scratch before the launches
+  tl::launch_range_work(sd.soff, G->WP.as<uint64_t>(), xb, xe, rw, s);
+  const uint64_t range_work = read_dev(rw, s);
   const tl::Tuning tu = effective_tuning(G->tuning, range_work);
   if (G->cached_alg == alg && G->cached_xb == xb && G->cached_xe == xe &&
       same_tuning(tu, G->used_tu))
@@ -583,6 +605,7 @@ tl_status tl_order_apply(tl_graph *G, const uint32_t *rank, int rank_on_device) 
   TL_API_BEGIN
   if (!G || !rank) tl::fail(TL_EINVAL, "graph or rank is NULL");
   G->cached_alg = -1;
+  G->wp_alg = -1;
   tl::build_dag(G->g, rank, rank_on_device != 0);
   TL_API_END
 }
@@ -671,6 +694,29 @@ void tl_count_hash_release(tl_count_hash_state *s) {
   }
 }
 
+tl_status tl_work_profile(tl_graph *G, tl_alg alg, uint32_t x_begin, uint32_t x_end,
+                          uint64_t *hist) {
+  TL_API_BEGIN
+  if (!G || !hist) tl::fail(TL_EINVAL, "graph or hist is NULL");
+  if (alg != TL_APP && alg != TL_APM && alg != TL_AMM)
+    tl::fail(TL_EINVAL, "alg must be TL_APP, TL_APM or TL_AMM");
+  ensure_ordered(G);
+  tl::DeviceGraph &g = G->g;
+  if (x_begin > x_end || x_end > g.n) tl::fail(TL_EINVAL, "seed range outside [0, n]");
+  cudaStream_t s = g.stream;
+  ensure_wp(G, alg);
+  const Sides sd = sides(g, alg);
+  constexpr uint64_t kBins = (uint64_t)tl::kProfileBinsP * tl::kProfileBinsW;
+  tl::DevBuf h(s);
+  h.reserve(kBins * 8);
+  TL_CUDA(cudaMemsetAsync(h.p, 0, kBins * 8, s));
+  tl::launch_work_profile(sd.poff, sd.soff, G->WP.as<uint64_t>(), x_begin, x_end,
+                          h.as<unsigned long long>(), s);
+  TL_CUDA(cudaMemcpyAsync(hist, h.p, kBins * 8, cudaMemcpyDeviceToHost, s));
+  TL_CUDA(cudaStreamSynchronize(s));
+  TL_API_END
+}
+
 tl_status tl_default_tuning(tl_tuning *out) {
   TL_API_BEGIN
   if (!out) tl::fail(TL_EINVAL, "out is NULL");
@@ -682,6 +728,10 @@ tl_status tl_set_tuning(tl_graph *G, const tl_tuning *t) {
   TL_API_BEGIN
   if (!G) tl::fail(TL_EINVAL, "graph is NULL");
   const tl_tuning v = t ? *t : tl_default_tuning_value();
+  if (v.small_max_p > tl::kSmallMaxP || v.medium_max_p > tl::kMediumMaxP ||
+      v.narrow_max_p > tl::kNarrowMaxP || v.mid_max_p > tl::kMidMaxP)
+    tl::fail(TL_EINVAL, "a probe-set threshold is above what its kernel's table holds "
+                        "(32, 1024, 256, 2048)");
   if (v.warp_work < 256 || v.warp_work > tl::kWarpWorkMax)
     tl::fail(TL_EINVAL, "warp_work must be in [256, 4096]");
   if (v.narrow_piece < 1024 || v.mid_piece < 1024 || v.large_min < 1024)

@@ -15,8 +15,9 @@
 // Every kernel walks the tests of a range with the same warp-level mapping
 // (scan_items): a window of 32 consecutive seed edges is held one per lane;
 // a list of at least 32 tests is streamed with 16-byte loads, shorter ones
-// share 32-test steps in which each lane finds its seed edge by a shuffle
-// binary search over the window, so all lanes work whatever the lengths.
+// share 128-test steps (four tests per lane) in which each lane finds the
+// seed edge of each of its tests by a shuffle binary search over the window,
+// so all lanes work whatever the lengths.
 // The seed edge of a range's first test is found by the whole warp (32
 // samples of WP and a ballot per round).
 //
@@ -165,32 +166,23 @@ __device__ __forceinline__ bool bucket_find(const uint32_t *H, int lgb, uint32_t
 // Filter bit of rank r (2^20 bits) for the hub tier's shared-memory filter.
 __device__ __forceinline__ uint32_t fslot(uint32_t r) { return (r * 0x85EBCA77u) >> 12; }
 
-// Membership tests of the walk: one(z) for a single key, check4 for the four
-// keys of a lane's 16-byte load, with the four first probes issued before any
-// result is used (the rare longer searches follow one by one).
+// Membership tests of the walk, four keys at a time (check4): the keys of a
+// lane's 16-byte load, or its four tests of a short-list step.  Where a probe
+// can miss its first slot, the four first probes are issued before any
+// result is used and the rare longer searches follow one by one.
 struct WarpHashMember {  // linear probing, per-warp table of 2^lg slots
   const uint32_t *H;
   int lg;
   __device__ bool one(uint32_t z) const { return hash_find(H, lg, z); }
   __device__ void check4(const uint32_t z[4], bool r[4]) const {
-    uint32_t h[4], v[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      h[u] = hslot(z[u], lg);
-      v[u] = H[h[u]];
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      r[u] = v[u] == z[u];
-      if (!r[u] && v[u] != kEmpty) r[u] = hash_find(H, lg, z[u]);
-    }
+    for (int u = 0; u < 4; ++u) r[u] = one(z[u]);
   }
 };
 
 struct BucketMember {  // four-slot buckets, 2^lgb buckets
   const uint32_t *H;
   int lgb;
-  __device__ bool one(uint32_t z) const { return bucket_find(H, lgb, z); }
   __device__ void check4(const uint32_t z[4], bool r[4]) const {
     uint4 q[4];
 #pragma unroll
@@ -539,7 +531,7 @@ __device__ __forceinline__ void scan_items(const ListArgs &a, uint64_t pb, uint6
   const unsigned lt = (1u << lane) - 1u;
   // seed edge holding test i0
   uint64_t k = (k0 != ~0ull) ? k0 : pb + warp_upper_bound_u64(a.WP + pb, pe - pb, i0) - 1;
-  uint64_t E = 0, A = 0, Elast = 0;
+  uint64_t E = 0, A = 0, Elast = 0, S = 0;  // S, E: first test and end of the lane's edge
   uint32_t iy = 0;
   auto load_window = [&](uint64_t kw) {
     const uint64_t kk = kw + lane;
@@ -555,32 +547,10 @@ __device__ __forceinline__ void scan_items(const ListArgs &a, uint64_t pb, uint6
       A = a.scan_off[y] - B;  // scanned element of test i is scan_adj[A + i]
       iy = a.inv[y];
     }
+    S = B;
     Elast = shfl_u64(E, 31);
   };
   load_window(k);
-  // append the warp's hits of one step to the slab
-  auto emit = [&](bool hit, uint32_t iyj, uint32_t z) {
-    const unsigned hm = __ballot_sync(0xffffffffu, hit);
-    if (!hm) return;
-    uint32_t basepos;
-    if (kEmit == 0) {
-      basepos = wcnt;
-      wcnt += __popc(hm);
-    } else {
-      basepos = o.cnt;
-      o.cnt += __popc(hm);
-    }
-    if (hit) {
-      const uint32_t r = basepos + __popc(hm & lt);
-      if (kEmit == 0) {
-        slab[3 * r + 0] = inv_x;
-        slab[3 * r + 1] = iyj;
-        slab[3 * r + 2] = z;
-      } else {
-        reinterpret_cast<uint2 *>(o.buf)[r] = make_uint2(iyj, z);
-      }
-    }
-  };
   uint64_t base = i0;
   while (base < i1) {
     // j0 = the window's seed edge holding test `base` (32: window exhausted)
@@ -670,29 +640,74 @@ __device__ __forceinline__ void scan_items(const ListArgs &a, uint64_t pb, uint6
       base += run;
       continue;
     }
-    // Short segments: one step of up to 32 tests spread over several lists.
+    // Short segments: one step of up to 128 tests spread over several lists,
+    // test base + 32 u + lane on lane `lane` (u = 0..3), so that each group of
+    // 32 is coalesced and every lane has four independent loads in flight.
+    // The step stops where a long list (>= 128 tests) starts, which the
+    // streaming path takes next.
     if (kEmit == 1 && o.cnt > kWarpBuf - kWarpStep) {
       if (!warp_commit(a, o, inv_x, base, probes, vf)) return;
     }
-    uint64_t lim = base + 32;
+    uint64_t lim = base + 128;
     if (lim > i1) lim = i1;
     if (lim > Elast) lim = Elast;
-    const uint32_t off = lane;
-    const bool act = base + off < lim;
-    // segment ends relative to base, clamped to [0, 64]
-    const uint32_t D = (E <= base) ? 0u : (uint32_t)((E - base) < 64 ? (E - base) : 64);
-    const int j = warp_count_le(D, off);  // seed edge of test base + lane (< 32 when act)
-    const int jj = j < 31 ? j : 31;
-    const uint64_t Aj = shfl_u64(A, jj);
-    const uint32_t iyj = __shfl_sync(0xffffffffu, iy, jj);
-    bool hit = false;
-    uint32_t z = 0;
-    if (act) {
-      z = a.scan_adj[Aj + base + off];
-      ++probes;
-      hit = member.one(z);
+    {
+      const bool long_after = E != ~0ull && S > base && E - S >= 128;
+      const unsigned lm = __ballot_sync(0xffffffffu, long_after);
+      if (lm) {
+        const uint64_t s0 = shfl_u64(S, __ffs(lm) - 1);
+        if (s0 < lim) lim = s0;
+      }
     }
-    emit(hit, iyj, z);
+    // segment ends relative to base, clamped to [0, 160]
+    const uint32_t D = (E <= base) ? 0u : (uint32_t)((E - base) < 160 ? (E - base) : 160);
+    uint32_t z[4], iyj[4];
+    bool act[4], hit[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const uint32_t off = lane + 32 * u;
+      act[u] = base + off < lim;
+      const int j = warp_count_le(D, off);  // seed edge of test base + off (< 32 when act)
+      const int jj = j < 31 ? j : 31;
+      const uint64_t Aj = shfl_u64(A, jj);
+      iyj[u] = __shfl_sync(0xffffffffu, iy, jj);
+      z[u] = act[u] ? a.scan_adj[Aj + base + off] : 0u;
+    }
+    member.check4(z, hit);
+    unsigned hm[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      hit[u] = hit[u] && act[u];
+      hm[u] = __ballot_sync(0xffffffffu, hit[u]);
+      probes += act[u] ? 1 : 0;
+    }
+    const uint32_t c0 = __popc(hm[0]), c1 = __popc(hm[1]), c2 = __popc(hm[2]);
+    const uint32_t total = c0 + c1 + c2 + __popc(hm[3]);
+    if (total > 0) {
+      uint32_t basepos;
+      if (kEmit == 0) {
+        basepos = wcnt;
+        wcnt += total;
+      } else {
+        basepos = o.cnt;
+        o.cnt += total;
+      }
+      const uint32_t startpos[4] = {basepos, basepos + c0, basepos + c0 + c1,
+                                    basepos + c0 + c1 + c2};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (hit[u]) {
+          const uint32_t r = startpos[u] + __popc(hm[u] & lt);
+          if (kEmit == 0) {
+            slab[3 * r + 0] = inv_x;
+            slab[3 * r + 1] = iyj[u];
+            slab[3 * r + 2] = z[u];
+          } else {
+            reinterpret_cast<uint2 *>(o.buf)[r] = make_uint2(iyj[u], z[u]);
+          }
+        }
+      }
+    }
     base = lim;
   }
 }
@@ -940,12 +955,13 @@ __global__ void k_classify(const uint64_t *__restrict__ poff, const uint64_t *__
     // every prescribed test runs, also when P_x is empty (possible for A--,
     // whose seeds are not its probe set): the work then equals the cost
     if (W > 0) {
-      if (p <= kSmallMaxP && W <= tu.warp_work) {
+      if (p <= tu.small_max_p && W <= tu.warp_work) {
         a0 = W + kVertexCost;
-      } else if (p <= kMediumMaxP && W <= tu.warp_work) {
+      } else if (p <= tu.medium_max_p && W <= tu.warp_work) {
         a1 = W + kVertexCost;
       } else {
-        const int tier = p <= kNarrowMaxP ? kTierNarrow : (p <= kMidMaxP ? kTierMid : kTierLarge);
+        const int tier =
+            p <= tu.narrow_max_p ? kTierNarrow : (p <= tu.mid_max_p ? kTierMid : kTierLarge);
         const uint64_t pw = piece_work(tu, tier, p);
         const uint64_t np = (W + pw - 1) / pw;
         if (tier == kTierNarrow) n2 = np; else if (tier == kTierMid) n3 = np; else n4 = np;
@@ -990,6 +1006,35 @@ __global__ void k_task_owner(const uint64_t *__restrict__ prefix, uint32_t x_beg
        r += (uint64_t)gridDim.x * blockDim.x) {
     for (uint64_t t = prefix[r]; t < prefix[r + 1]; ++t) task_x[t] = x_begin + (uint32_t)r;
   }
+}
+
+__global__ void k_range_work(const uint64_t *__restrict__ soff, const uint64_t *__restrict__ WP,
+                             uint32_t x_begin, uint32_t x_end, uint64_t *__restrict__ out) {
+  *out = WP[soff[x_end]] - WP[soff[x_begin]];
+}
+
+// Per-block bins in shared memory, added to the global histogram at the end.
+__global__ void k_work_profile(const uint64_t *__restrict__ poff, const uint64_t *__restrict__ soff,
+                               const uint64_t *__restrict__ WP, uint32_t x_begin, uint32_t x_end,
+                               unsigned long long *__restrict__ hist) {
+  __shared__ unsigned long long bins[kProfileBinsP * kProfileBinsW];
+  for (int i = threadIdx.x; i < kProfileBinsP * kProfileBinsW; i += blockDim.x) bins[i] = 0;
+  __syncthreads();
+  const uint64_t nr = x_end - x_begin;
+  for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < nr;
+       r += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t x = x_begin + (uint32_t)r;
+    const uint64_t W = WP[soff[x + 1]] - WP[soff[x]];
+    if (W == 0) continue;
+    const uint64_t p = poff[x + 1] - poff[x];
+    const int bp = 64 - __clzll((long long)p), bw = 64 - __clzll((long long)W);
+    atomicAdd(&bins[(bp < kProfileBinsP ? bp : kProfileBinsP - 1) * kProfileBinsW +
+                    (bw < kProfileBinsW ? bw : kProfileBinsW - 1)],
+              (unsigned long long)W);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kProfileBinsP * kProfileBinsW; i += blockDim.x)
+    if (bins[i]) atomicAdd(&hist[i], bins[i]);
 }
 
 template <class K>
@@ -1043,6 +1088,21 @@ void launch_task_owner(const uint64_t *piece_prefix, uint32_t x_begin, uint64_t 
                        uint32_t *task_x, cudaStream_t s) {
   if (nr == 0) return;
   k_task_owner<<<grid_for(nr, 256), 256, 0, s>>>(piece_prefix, x_begin, nr, task_x);
+  TL_CHECK_LAUNCH();
+}
+
+void launch_range_work(const uint64_t *soff, const uint64_t *WP, uint32_t x_begin,
+                       uint32_t x_end, uint64_t *out, cudaStream_t s) {
+  k_range_work<<<1, 1, 0, s>>>(soff, WP, x_begin, x_end, out);
+  TL_CHECK_LAUNCH();
+}
+
+void launch_work_profile(const uint64_t *poff, const uint64_t *soff, const uint64_t *WP,
+                         uint32_t x_begin, uint32_t x_end, unsigned long long *hist,
+                         cudaStream_t s) {
+  if (x_end <= x_begin) return;
+  k_work_profile<<<grid_for((uint64_t)(x_end - x_begin), 256, (unsigned)num_sms() * 2), 256, 0,
+                   s>>>(poff, soff, WP, x_begin, x_end, hist);
   TL_CHECK_LAUNCH();
 }
 

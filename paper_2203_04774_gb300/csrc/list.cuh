@@ -33,6 +33,10 @@ constexpr uint64_t kVertexCost = 256;
 
 // Run-time choices of the work split (tl_tuning in the C ABI).
 struct Tuning {
+  uint32_t small_max_p;  // tier thresholds on p, at most the table sizes allow:
+  uint32_t medium_max_p; //   small <= kSmallMaxP, medium <= kMediumMaxP,
+  uint32_t narrow_max_p; //   narrow <= kNarrowMaxP, mid <= kMidMaxP
+  uint32_t mid_max_p;
   uint32_t warp_work;    // warp-tier task size, tests (256 .. kWarpWorkMax)
   uint32_t narrow_piece; // tests per piece of a narrow vertex
   uint32_t mid_piece;    // tests per piece of a mid vertex
@@ -157,6 +161,16 @@ void launch_compact_tier(const uint32_t *flags, const uint64_t *pos, const uint6
 void launch_task_bounds(const uint64_t *wp_list, uint64_t count, uint64_t n_tasks,
                         uint64_t warp_work, uint32_t *task_start, cudaStream_t s);
 // task_x[t] = the vertex owning task t of a narrow, mid or large tier.
+// Work profile of the B vertices x in [x_begin, x_end): hist[bp * kProfileBinsW
+// + bw] += W_x, bp = bit length of p_x, bw = bit length of W_x (hist is
+// kProfileBinsP * kProfileBinsW uint64 on the device, zeroed by the caller).
+constexpr int kProfileBinsP = TL_PROFILE_BINS_P, kProfileBinsW = TL_PROFILE_BINS_W;
+void launch_work_profile(const uint64_t *poff, const uint64_t *soff, const uint64_t *WP,
+                         uint32_t x_begin, uint32_t x_end, unsigned long long *hist,
+                         cudaStream_t s);
+// *out = WP[soff[x_end]] - WP[soff[x_begin]]: the tests of a seed range.
+void launch_range_work(const uint64_t *soff, const uint64_t *WP, uint32_t x_begin,
+                       uint32_t x_end, uint64_t *out, cudaStream_t s);
 void launch_task_owner(const uint64_t *piece_prefix, uint32_t x_begin, uint64_t nr,
                        uint32_t *task_x, cudaStream_t s);
 // tier 0, 1: warp kernels; tier 2: narrow (one-warp) CTA kernel; tier 3: mid

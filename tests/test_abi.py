@@ -87,7 +87,9 @@ def test_union_and_server_arguments_rejected_without_gpu(built):
 
 def test_tuning_defaults_and_argument_checks_without_gpu(built):
     t = tl.tl_default_tuning()
-    assert t == {"warp_work": 4096, "narrow_piece": 1 << 14, "mid_piece": 1 << 16,
+    assert t == {"small_max_p": 32, "medium_max_p": 1024, "narrow_max_p": 256,
+                 "mid_max_p": 2048, "warp_work": 4096, "narrow_piece": 1 << 14,
+                 "mid_piece": 1 << 16,
                  "large_per_p": 64, "large_min": 1 << 16, "large_max": 1 << 22}
     assert built.tl_set_tuning(None, None) == tl.TL_EINVAL
     out = tl.Tuning()

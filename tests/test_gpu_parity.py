@@ -391,11 +391,14 @@ def test_device_generator_on_gpu_matches_host():
      "large_min": 1024, "large_max": 1024},
     {"warp_work": 1024, "narrow_piece": 1 << 20, "mid_piece": 1 << 22, "large_per_p": 4096,
      "large_min": 1 << 16, "large_max": 1 << 26},
+    {"small_max_p": 4, "medium_max_p": 40, "narrow_max_p": 16, "mid_max_p": 100},
+    {"small_max_p": 0, "medium_max_p": 0, "narrow_max_p": 0, "mid_max_p": 0},
 ])
 def test_tuning_changes_speed_not_results(tuning):
     """The work split (tl_set_tuning) changes task shapes only: extreme piece
-    sizes and warp-task sizes list the oracle's triangle set with probes =
-    C++ / C+- / C-- (Property 1)."""
+    sizes, warp-task sizes and probe-set thresholds (down to every vertex in
+    the large kernel) list the oracle's triangle set with probes = C++ / C+- /
+    C-- (Property 1)."""
     n = 30000
     e = np.concatenate([synth.chung_lu(n, 30, 2.1, 31), synth.complete(90)])
     rank = synth.order_degree(synth.simple_csr(n, e)[0])
@@ -404,7 +407,7 @@ def test_tuning_changes_speed_not_results(tuning):
     ref = oracle.Graph(n, e)
     ref.order_apply(rank)
     tl.tl_set_tuning(g.h, tuning)
-    assert tl.tl_get_tuning(g.h) == tuning
+    assert tl.tl_get_tuning(g.h) == dict(tl.tl_default_tuning(), **tuning)
     for alg in (tl.TL_APP, tl.TL_APM, tl.TL_AMM):
         t, nt, probes, _ = g.list_collect(alg, tl.TL_MIN_CHUNK_BYTES)
         rt, rc, rh, rp = ref.list(alg)
