@@ -731,8 +731,13 @@ def run_serve(args, requests: int) -> dict:
         al = (synth.counter_uniform(cfg["seed"], 31, R) < 0.5).astype(np.int64)
         return arr, gi, oi, al
 
-    def serve(arr, gi, oi, al, max_batch, workers):
+    from paper_2203_04774_gb300 import autotune
+    table = autotune.load_table()
+
+    def serve(arr, gi, oi, al, max_batch, workers, tuned=False):
         srv = tl.Server(budget, max_batch=max_batch, workers=workers)
+        if tuned:  # work splits per batch group, by its degree profile
+            srv.set_tuning_table(table)
         ids = []
         for g, rs in zip(graphs, ranks):
             gid = srv.add_graph(g)
@@ -785,11 +790,14 @@ def run_serve(args, requests: int) -> dict:
     rows = []
     for rate in cfg["rates_per_s"]:
         arr, gi, oi, al = requests(rate)
-        b, rb = serve(arr, gi, oi, al, 256, 2)
+        b, rb = serve(arr, gi, oi, al, 256, 2, tuned=True)
+        f, rf = serve(arr, gi, oi, al, 256, 2, tuned=False)
         p, rp = serve(arr, gi, oi, al, 1, 1)
-        assert rb == rp, "a request's result depends on its batch"
-        rows.append({"rate_per_s": rate, "batched": b, "per_request": p,
-                     "throughput_ratio": b["requests_per_s"] / p["requests_per_s"]})
+        assert rb == rp == rf, "a request's result depends on its batch or work split"
+        rows.append({"rate_per_s": rate, "batched": b, "batched_fixed_split": f,
+                     "per_request": p,
+                     "throughput_ratio": b["requests_per_s"] / p["requests_per_s"],
+                     "autotune_gain": b["requests_per_s"] / f["requests_per_s"]})
         log(f"[bench] rate {rate}: batched {b} per-request {p}")
     launches = tl.tl_kernel_launches() - launches0
     clk = clocks.stop()
@@ -801,7 +809,10 @@ def run_serve(args, requests: int) -> dict:
         "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (seeded Chung-Lu pool generated on the device, Poisson arrivals)",
         "config": dict(cfg, pool_edges=int(sum(ms)), hbm_budget_bytes=budget,
-                       batched={"max_batch": 256, "workers": 2},
+                       batched={"max_batch": 256, "workers": 2,
+                                "work_split": "per batch group, nearest tuning-table profile"},
+                       batched_fixed_split={"max_batch": 256, "workers": 2,
+                                            "work_split": "library defaults"},
                        per_request={"max_batch": 1, "workers": 1}),
         "rates": rows, "equal_output": True, "gpu_launches": launches, "clocks": clk,
     }

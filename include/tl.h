@@ -223,7 +223,7 @@ TL_EXPORT tl_status tl_list_triangles_range(tl_graph *g, tl_alg alg, uint32_t x_
 typedef struct {
   uint32_t small_max_p;  /* <= 32   (per-warp table of 64 slots) */
   uint32_t medium_max_p; /* <= 1024 (per-warp table of 2048 slots) */
-  uint32_t narrow_max_p; /* <= 256  (per-CTA table of 1024 slots) */
+  uint32_t narrow_max_p; /* <= 256  (per-CTA table of 512 slots behind a filter) */
   uint32_t mid_max_p;    /* <= 2048 (per-CTA table of 8192 slots) */
   uint32_t warp_work;    /* 256 .. 4096 */
   uint32_t narrow_piece; /* >= 1024 */
@@ -371,6 +371,7 @@ typedef struct {
   uint64_t t_submit_ns;  /* tl_server_now_ns() at submit, admission and completion */
   uint64_t t_admit_ns;
   uint64_t t_done_ns;
+  int32_t tuning_entry;  /* entry of the tuning table used for its group, -1 = defaults */
 } tl_request_result;
 TL_EXPORT tl_status tl_server_create(tl_server **out, const tl_server_config *cfg);
 /* Register g (caller-owned, loaded on the current device) -> *graph_id. */
@@ -381,6 +382,24 @@ TL_EXPORT tl_status tl_server_add_graph(tl_server *s, const tl_graph *g, uint32_
  * device memory until tl_server_free).  Not a permutation -> TL_EINVAL. */
 TL_EXPORT tl_status tl_server_add_ordering(tl_server *s, uint32_t graph_id, const uint32_t *rank,
                                            int rank_on_device, uint32_t *ordering_id);
+/* Work splits by degree profile for the server's batches (see tl_tuning and
+ * tl_work_profile): before each algorithm group of a batch is listed, its
+ * work profile is computed on the device and the group takes the tuning of
+ * the nearest entry of the same algorithm, the distance being the L1
+ * distance of the normalised profile marginals (by bit length of p and of
+ * W) plus |log2 m - log2_m| / 8, m the batch's edge count.  count = 0 (or
+ * entries NULL) restores the defaults.  The table is copied; it applies to
+ * batches that start after the call.  Entries are those of
+ * paper_2203_04774_gb300/tuning_table.json (autotune.py). */
+typedef struct {
+  tl_alg alg;
+  double profile_p[TL_PROFILE_BINS_P];
+  double profile_w[TL_PROFILE_BINS_W];
+  double log2_m;
+  tl_tuning tuning;
+} tl_tuning_entry;
+TL_EXPORT tl_status tl_server_set_tuning_table(tl_server *s, const tl_tuning_entry *entries,
+                                               uint32_t count);
 /* Queue a request; returns at once with its id. */
 TL_EXPORT tl_status tl_server_submit(tl_server *s, uint32_t graph_id, uint32_t ordering_id,
                                      tl_alg alg, uint64_t *request_id);

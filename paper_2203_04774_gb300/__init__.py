@@ -53,7 +53,8 @@ class ServerConfig(ctypes.Structure):
 
 class RequestResult(ctypes.Structure):
     _fields_ = [("status", _I), ("batch_size", _U32), ("triangles", _U64), ("hash", _U64),
-                ("t_submit_ns", _U64), ("t_admit_ns", _U64), ("t_done_ns", _U64)]
+                ("t_submit_ns", _U64), ("t_admit_ns", _U64), ("t_done_ns", _U64),
+                ("tuning_entry", ctypes.c_int32)]
 
 
 TL_KERNELS = 5  # small, medium, narrow, mid, large
@@ -76,6 +77,13 @@ class Tuning(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {name: int(getattr(self, name)) for name, _ in self._fields_}
+
+
+class TuningEntry(ctypes.Structure):
+    """tl_tuning_entry: one row of a server's work-split table."""
+    _fields_ = [("alg", _I), ("profile_p", ctypes.c_double * 33),
+                ("profile_w", ctypes.c_double * 48), ("log2_m", ctypes.c_double),
+                ("tuning", Tuning)]
 
 
 SIGNATURES = {
@@ -103,6 +111,7 @@ SIGNATURES = {
     "tl_server_wait": ([_P, _U64, ctypes.POINTER(RequestResult)], _I),
     "tl_server_footprint": ([_P, _U32, ctypes.POINTER(_U64), ctypes.POINTER(_U64)], _I),
     "tl_server_free": ([_P], None),
+    "tl_server_set_tuning_table": ([_P, _P, _U32], _I),
     "tl_server_now_ns": ([], _U64),
     "tl_count_hash_noalloc": ([_P, _U64, _U64, _P], _I),
     "tl_count_hash_parts": ([_P, _U64, _U64, _P], _I),
@@ -573,6 +582,27 @@ class Server:
                "tl_server_footprint")
         return int(r.value), int(b.value)
 
+    def set_tuning_table(self, entries: list | None) -> None:
+        """Work splits by degree profile for later batches: entries in the form
+        of autotune.py's table (None or [] restores the defaults)."""
+        names = {"A++": TL_APP, "A+-": TL_APM, "A--": TL_AMM}
+        arr = (TuningEntry * max(1, len(entries or [])))()
+        defaults = Tuning()
+        _check(lib().tl_default_tuning(ctypes.byref(defaults)), "tl_default_tuning")
+        for k, e in enumerate(entries or []):
+            arr[k].alg = names[e["alg"]]
+            for i, v in enumerate(e["profile"]["p"]):
+                arr[k].profile_p[i] = v
+            for i, v in enumerate(e["profile"]["w"]):
+                arr[k].profile_w[i] = v
+            arr[k].log2_m = float(np.log2(max(e["profile"]["m"], 1)))
+            t = Tuning.from_buffer_copy(defaults)
+            for f, v in e["tuning"].items():
+                setattr(t, f, int(v))
+            arr[k].tuning = t
+        _check(lib().tl_server_set_tuning_table(self.h, arr, len(entries or [])),
+               "tl_server_set_tuning_table")
+
     def submit(self, graph_id: int, ordering_id: int, alg: int) -> int:
         rid = _U64()
         _check(lib().tl_server_submit(self.h, graph_id, ordering_id, alg, ctypes.byref(rid)),
@@ -585,7 +615,7 @@ class Server:
         return {"status": int(r.status), "batch_size": int(r.batch_size),
                 "triangles": int(r.triangles), "hash": int(r.hash),
                 "t_submit_ns": int(r.t_submit_ns), "t_admit_ns": int(r.t_admit_ns),
-                "t_done_ns": int(r.t_done_ns)}
+                "t_done_ns": int(r.t_done_ns), "tuning_entry": int(r.tuning_entry)}
 
     @staticmethod
     def now_ns() -> int:

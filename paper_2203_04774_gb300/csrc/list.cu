@@ -216,6 +216,19 @@ struct FilterMember {  // one bit per hashed rank: may answer yes wrongly
   }
 };
 
+struct SmallFilterMember {  // 2^14 bits, one hashed bit per key: may answer yes wrongly
+  const uint32_t *F;
+  __device__ static uint32_t bit(uint32_t z) { return (z * 0x85EBCA77u) >> 18; }
+  __device__ bool one(uint32_t z) const {
+    const uint32_t f = bit(z);
+    return ((F[f >> 5] >> (f & 31)) & 1u) != 0;
+  }
+  __device__ void check4(const uint32_t z[4], bool r[4]) const {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) r[u] = one(z[u]);
+  }
+};
+
 struct SortedRowMember {  // binary search in the sorted probe list
   const uint32_t *P;
   uint64_t n;
@@ -290,14 +303,47 @@ struct WarpOut {
 // Exact-membership checks applied to a warp's staged entries before they are
 // written.  NoVerify: the walk's test was exact already.  GlobalHashVerify:
 // the walk tested a shared-memory filter only; the CTA's hash table in global
-// memory decides, four keys per lane in flight.
+// memory decides, four keys per lane in flight.  SharedBucketVerify: the walk
+// tested a small shared filter; the bucketed table behind it decides, in a
+// function of its own so that the walk keeps its registers.
 struct NoVerify {
   static constexpr bool kActive = false;
-  __device__ void check4(const uint32_t *, const bool *, bool *) const {}
+};
+
+__device__ __noinline__ uint32_t verify_bucket(uint32_t *buf, uint32_t cnt, const uint32_t *H,
+                                               int lgb) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  uint2 *b2 = reinterpret_cast<uint2 *>(buf);
+  uint32_t out = 0;
+  for (uint32_t i0 = 0; i0 < cnt; i0 += 32) {
+    const uint32_t i = i0 + lane;
+    uint2 e = make_uint2(0, 0);
+    bool keep = false;
+    if (i < cnt) {
+      e = b2[i];
+      keep = bucket_find(H, lgb, e.y);
+    }
+    const unsigned km = __ballot_sync(0xffffffffu, keep);
+    __syncwarp();  // every entry of this round is read before any is moved
+    if (keep) b2[out + __popc(km & lt)] = e;
+    out += __popc(km);
+    __syncwarp();
+  }
+  return out;
+}
+
+struct SharedBucketVerify {
+  static constexpr bool kActive = true, kOutOfLine = true;
+  const uint32_t *H;
+  int lgb;
+  __device__ uint32_t run(uint32_t *buf, uint32_t cnt) const {
+    return verify_bucket(buf, cnt, H, lgb);
+  }
 };
 
 struct GlobalHashVerify {
-  static constexpr bool kActive = true;
+  static constexpr bool kActive = true, kOutOfLine = false;
   const uint32_t *H;
   int lg;
   __device__ void check4(const uint32_t z[4], const bool valid[4], bool res[4]) const {
@@ -336,8 +382,7 @@ struct GlobalHashVerify {
 // Keep the staged entries (original id of y, rank of z) whose z passes the
 // exact check, compacted in place; returns how many are left.
 template <class Verify>
-__device__ __forceinline__ uint32_t warp_verify(uint32_t *buf, uint32_t cnt, const Verify &vf) {
-  if (!Verify::kActive) return cnt;
+__device__ __forceinline__ uint32_t warp_verify_4(uint32_t *buf, uint32_t cnt, const Verify &vf) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   uint2 *b2 = reinterpret_cast<uint2 *>(buf);
@@ -364,6 +409,17 @@ __device__ __forceinline__ uint32_t warp_verify(uint32_t *buf, uint32_t cnt, con
     __syncwarp();
   }
   return out;
+}
+
+template <class Verify>
+__device__ __forceinline__ uint32_t warp_verify(uint32_t *buf, uint32_t cnt, const Verify &vf) {
+  if constexpr (!Verify::kActive) {
+    return cnt;
+  } else if constexpr (Verify::kOutOfLine) {
+    return vf.run(buf, cnt);
+  } else {
+    return warp_verify_4(buf, cnt, vf);
+  }
 }
 
 // Copy a warp's buffer of cnt > 0 entries (original id of y, rank of z) to
@@ -452,6 +508,17 @@ __device__ __forceinline__ bool warp_commit(const ListArgs &a, WarpOut &o, uint3
   o.safe = cur;
   o.probes_safe = probes;
   return true;
+}
+
+// A piece's tests split evenly (32-aligned) over kWarps warps.
+template <int kWarps, class T>
+__device__ __forceinline__ void split_piece(uint64_t ia, uint64_t ib, T r[][2]) {
+  const uint64_t per = (((ib - ia) + kWarps - 1) / kWarps + 31) & ~31ull;
+  for (int w = 0; w < kWarps; ++w) {
+    const uint64_t u = ia + (uint64_t)w * per, v = u + per;
+    r[w][0] = u < ib ? u : ib;
+    r[w][1] = v < ib ? v : ib;
+  }
 }
 
 // Next piece of work of a CTA tier (thread 0): a retry piece (*retry set to
@@ -761,7 +828,7 @@ __global__ void __launch_bounds__(kWarpThreads, 4) k_list_warp(ListArgs a) {
 //   sorted row (mode 2).
 
 template <int THREADS, int TIER>
-__global__ void __launch_bounds__(THREADS, TIER == kTierLarge ? 1 : (TIER == kTierMid ? 4 : 32))
+__global__ void __launch_bounds__(THREADS, TIER == kTierLarge ? 1 : (TIER == kTierMid ? 4 : 28))
     k_list_cta(ListArgs a) {
   // probe structure (bitmap, hash or filter) | one output buffer per warp
   extern __shared__ __align__(16) uint32_t sm[];
@@ -796,12 +863,7 @@ __global__ void __launch_bounds__(THREADS, TIER == kTierLarge ? 1 : (TIER == kTi
         s_rng[w][1] = w < (int)nr ? rp->r[w][1] : 0;
       }
     } else {  // the piece's tests, split evenly (32-aligned) over the warps
-      const uint64_t per = (((ib - ia) + kWarps - 1) / kWarps + 31) & ~31ull;
-      for (int w = 0; w < kWarps; ++w) {
-        const uint64_t u = ia + (uint64_t)w * per, v = u + per;
-        s_rng[w][0] = u < ib ? u : ib;
-        s_rng[w][1] = v < ib ? v : ib;
-      }
+      split_piece<kWarps>(ia, ib, s_rng);
     }
     const uint64_t p = a.poff[x + 1] - a.poff[x];
     s_x = x;
@@ -849,6 +911,17 @@ __global__ void __launch_bounds__(THREADS, TIER == kTierLarge ? 1 : (TIER == kTi
         const uint32_t r = a.padj[q];
         atomicOr(&sm[r >> 5], 1u << (r & 31));
       }
+    } else if (TIER == kTierNarrow) {  // filter words, then the buckets
+      for (uint32_t i = threadIdx.x; i < (uint32_t)kNarrowFilterWords; i += THREADS) sm[i] = 0;
+      for (uint32_t i = threadIdx.x; i < (1u << lg); i += THREADS)
+        sm[kNarrowFilterWords + i] = kEmpty;
+      __syncthreads();
+      for (uint64_t q = pb + threadIdx.x; q < pe; q += THREADS) {
+        const uint32_t r = a.padj[q];
+        const uint32_t f = SmallFilterMember::bit(r);
+        atomicOr(&sm[f >> 5], 1u << (f & 31));
+        bucket_insert(sm + kNarrowFilterWords, lg - 2, r);
+      }
     } else if (mode == 1) {  // lg = log2(slots); buckets of four
       for (uint32_t i = threadIdx.x; i < (1u << lg); i += THREADS) sm[i] = kEmpty;
       __syncthreads();
@@ -873,7 +946,13 @@ __global__ void __launch_bounds__(THREADS, TIER == kTierLarge ? 1 : (TIER == kTi
     o.safe = wa;
     o.probes_safe = 0;
     o.failed = false;
-    if (kLarge && mode == 0) {
+    if (TIER == kTierNarrow) {
+      // the walk tests the filter; staged candidates meet the table at flush
+      const SharedBucketVerify vf{sm + kNarrowFilterWords, lg - 2};
+      scan_items<1, kPf>(a, sb, se, ~0ull, wa, wb, inv_x, SmallFilterMember{sm}, nullptr, o,
+                         unused, probes, vf);
+      if (!o.failed) warp_commit(a, o, inv_x, wb, probes, vf);
+    } else if (kLarge && mode == 0) {
       scan_items<1, kPf>(a, sb, se, ~0ull, wa, wb, inv_x, BitmapMember{sm}, nullptr, o, unused,
                          probes);
     } else if (!kLarge || mode == 1) {
@@ -890,7 +969,8 @@ __global__ void __launch_bounds__(THREADS, TIER == kTierLarge ? 1 : (TIER == kTi
       scan_items<1, kPf>(a, sb, se, ~0ull, wa, wb, inv_x,
                          SortedRowMember{a.padj + pb, pe - pb}, nullptr, o, unused, probes);
     }
-    if (!o.failed && (!kLarge || mode != 3)) warp_commit(a, o, inv_x, wb, probes, NoVerify());
+    if (!o.failed && TIER != kTierNarrow && (!kLarge || mode != 3))
+      warp_commit(a, o, inv_x, wb, probes, NoVerify());
     // commit the warp's tests before o.safe; queue the rest for the next launch
     unsigned long long done = o.probes_safe;
 #pragma unroll

@@ -9,7 +9,8 @@ namespace tl {
 // number of membership tests of x; ww = Tuning::warp_work):
 //   0 small:  p <= 32,   W <= ww  -- one warp per x, 64-slot hash per warp
 //   1 medium: p <= 1024, W <= ww  -- one warp per x, 2048-slot hash per warp
-//   2 narrow: p <= 256,  W >  ww  -- one-warp CTA per piece, 1024-slot bucketed hash
+//   2 narrow: p <= 256,  W >  ww  -- one-warp CTA per piece, 2^14-bit filter in
+//                                    front of a 512-slot bucketed hash
 //   3 mid:    p <= 2048, W >  ww  -- 256-thread CTA per piece, 8192-slot bucketed hash
 //   4 large:  p >  2048           -- 1024-thread CTA per piece, bitmap / hash
 constexpr int kTiers = 5;
@@ -20,7 +21,8 @@ constexpr int kMidThreads = 256;
 constexpr int kLargeThreads = 1024;
 constexpr uint32_t kSmallMaxP = 32, kMediumMaxP = 1024, kNarrowMaxP = 256, kMidMaxP = 2048;
 constexpr int kSmallSlots = 64, kMediumSlots = 2048;  // per warp, >= 2p (load <= 1/2)
-constexpr int kNarrowSlots = 1024;                     // per one-warp CTA, >= 4p
+constexpr int kNarrowSlots = 512;                      // per one-warp CTA, >= 2p
+constexpr int kNarrowFilterWords = 512;                // 2^14 filter bits before the table
 constexpr int kMidSlots = 8192;                        // per CTA, >= 4p
 // Work (membership tests) per task: a warp-tier task is owned by one warp
 // and groups vertices up to about warp_work units, a vertex weighing its
@@ -65,7 +67,7 @@ constexpr uint32_t kGHashSlots = 1u << 18;
 // (one step adds at most kWarpStep hits) and at the end of its range.
 constexpr uint32_t kWarpBuf = 352;  // 4 mid CTAs (56 KiB each) per SM
 constexpr uint32_t kWarpStep = 128;
-constexpr int kNarrowProbeBytes = kNarrowSlots * 4;
+constexpr int kNarrowProbeBytes = (kNarrowFilterWords + kNarrowSlots) * 4;
 constexpr int kMidProbeBytes = kMidSlots * 4;
 constexpr int kLargeProbeBytes = (int)(kBitmapMaxN / 8);  // = kHashMaxSlots * 4 = kFilterWords * 4
 constexpr int kNarrowSmemBytes = kNarrowProbeBytes + (kNarrowThreads / 32) * (int)kWarpBuf * 8;

@@ -9,6 +9,8 @@
 // estimated footprint against the budget and releases it when the batch ends.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
+#include <memory>
 #include <condition_variable>
 #include <deque>
 #include <mutex>
@@ -71,11 +73,55 @@ struct tl_server {
   uint64_t in_use = 0, next_id = 1;
   bool stop = false;
   std::vector<Worker> workers;
+  // work splits by degree profile; replaced whole, read by workers under mu
+  std::shared_ptr<const std::vector<tl_tuning_entry>> tuning;
 };
 
 namespace {
 
 uint64_t footprint(uint32_t n, uint64_t m) { return 40 * m + 160 * (uint64_t)n; }
+
+// The entry of `table` for `alg` nearest to the work profile of ranks
+// [xb, xe) of u (see tl_server_set_tuning_table), or -1.
+int nearest_entry(tl_graph *u, tl_alg alg, uint32_t xb, uint32_t xe,
+                  const std::vector<tl_tuning_entry> &table, tl_status &st) {
+  bool any = false;
+  for (const auto &e : table) any = any || e.alg == alg;
+  if (!any) return -1;
+  std::vector<uint64_t> h((size_t)TL_PROFILE_BINS_P * TL_PROFILE_BINS_W);
+  st = tl_work_profile(u, alg, xb, xe, h.data());
+  if (st != TL_OK) return -1;
+  double p[TL_PROFILE_BINS_P] = {}, w[TL_PROFILE_BINS_W] = {}, tot = 0;
+  for (int i = 0; i < TL_PROFILE_BINS_P; ++i)
+    for (int j = 0; j < TL_PROFILE_BINS_W; ++j) {
+      const double v = (double)h[(size_t)i * TL_PROFILE_BINS_W + j];
+      p[i] += v;
+      w[j] += v;
+      tot += v;
+    }
+  if (tot > 0) {
+    for (double &v : p) v /= tot;
+    for (double &v : w) v /= tot;
+  }
+  uint32_t n = 0;
+  uint64_t m = 0;
+  tl_graph_size(u, &n, &m);
+  const double lm = std::log2((double)(m ? m : 1));
+  int best = -1;
+  double bd = 0;
+  for (size_t k = 0; k < table.size(); ++k) {
+    const tl_tuning_entry &e = table[k];
+    if (e.alg != alg) continue;
+    double d = std::fabs(lm - e.log2_m) / 8.0;
+    for (int i = 0; i < TL_PROFILE_BINS_P; ++i) d += std::fabs(p[i] - e.profile_p[i]);
+    for (int j = 0; j < TL_PROFILE_BINS_W; ++j) d += std::fabs(w[j] - e.profile_w[j]);
+    if (best < 0 || d < bd) {
+      best = (int)k;
+      bd = d;
+    }
+  }
+  return best;
+}
 
 // Runs one batch on worker W; fills every request's result (not `done`).
 void run_batch(tl_server *S, Worker &W, std::vector<Request *> &batch) {
@@ -102,13 +148,25 @@ void run_batch(tl_server *S, Worker &W, std::vector<Request *> &batch) {
               cudaMemsetAsync(W.d_hashes, 0, k * 8, W.cstream) == cudaSuccess &&
               cudaStreamSynchronize(W.cstream) == cudaSuccess;
     if (!ok) st = TL_ECUDA;
-    // one listing range per run of requests with the same algorithm
+    std::shared_ptr<const std::vector<tl_tuning_entry>> table;
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      table = S->tuning;
+    }
+    // one listing range per run of requests with the same algorithm, under
+    // the work split of the table entry nearest to that range's profile
     for (uint32_t i = 0; st == TL_OK && i < k;) {
       uint32_t j = i;
       while (j < k && batch[j]->alg == batch[i]->alg) ++j;
-      st = tl_list_triangles_range(u, batch[i]->alg, (uint32_t)vb[i], (uint32_t)vb[j],
-                                   S->cfg.chunk_bytes, tl_count_hash_parts, &cs, nullptr,
-                                   nullptr);
+      int e = -1;
+      if (table && !table->empty())
+        e = nearest_entry(u, batch[i]->alg, (uint32_t)vb[i], (uint32_t)vb[j], *table, st);
+      if (st == TL_OK) st = tl_set_tuning(u, e >= 0 ? &(*table)[e].tuning : nullptr);
+      for (uint32_t q = i; q < j; ++q) batch[q]->res.tuning_entry = e;
+      if (st == TL_OK)
+        st = tl_list_triangles_range(u, batch[i]->alg, (uint32_t)vb[i], (uint32_t)vb[j],
+                                     S->cfg.chunk_bytes, tl_count_hash_parts, &cs, nullptr,
+                                     nullptr);
       i = j;
     }
     if (st == TL_OK) {
@@ -322,6 +380,7 @@ tl_status tl_server_submit(tl_server *S, uint32_t graph_id, uint32_t ordering_id
     tl::fail(TL_EINVAL, "alg must be TL_APP, TL_APM or TL_AMM");
   Request *r = new Request();
   r->res.t_submit_ns = now_ns();
+  r->res.tuning_entry = -1;
   {
     std::lock_guard<std::mutex> lk(S->mu);
     if (graph_id >= S->graphs.size() || ordering_id >= S->graphs[graph_id].prepared.size()) {
@@ -339,6 +398,22 @@ tl_status tl_server_submit(tl_server *S, uint32_t graph_id, uint32_t ordering_id
     *request_id = r->id;
   }
   S->cv_work.notify_one();
+  TL_SERVE_END
+}
+
+tl_status tl_server_set_tuning_table(tl_server *S, const tl_tuning_entry *entries,
+                                     uint32_t count) {
+  TL_SERVE_BEGIN
+  if (!S) tl::fail(TL_EINVAL, "server is NULL");
+  auto t = std::make_shared<std::vector<tl_tuning_entry>>();
+  if (entries && count) {
+    t->assign(entries, entries + count);
+    for (const auto &e : *t)
+      if (e.alg != TL_APP && e.alg != TL_APM && e.alg != TL_AMM)
+        tl::fail(TL_EINVAL, "a tuning entry names an unknown algorithm");
+  }
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->tuning = t;
   TL_SERVE_END
 }
 

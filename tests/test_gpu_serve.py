@@ -187,3 +187,43 @@ def test_one_waiter_per_request(pool):
     assert errs == [tl.TL_EINVAL] and len(got) == 1
     assert (got[0]["triangles"], got[0]["hash"]) == want[(0, tl.TL_APM)]
     srv.close()
+
+
+def test_tuning_table_by_profile(pool):
+    """With a table of work splits the server picks, per algorithm group of a
+    batch, the entry nearest to the group's work profile: results stay the
+    oracle's, and a one-request batch takes the entry autotune.nearest picks
+    for that graph alone."""
+    import torch
+
+    from paper_2203_04774_gb300 import autotune
+
+    def entry(alg, p_bin, tuning):
+        p = np.zeros(tl.TL_PROFILE_BINS_P)
+        w = np.zeros(tl.TL_PROFILE_BINS_W)
+        p[p_bin] = 1.0
+        w[12] = 1.0
+        return {"alg": alg, "tuning": tuning,
+                "profile": {"p": p.tolist(), "w": w.tolist(), "m": 1 << 16, "n": 1 << 12}}
+    table = [entry("A++", 3, {"warp_work": 256, "narrow_piece": 1024}),
+             entry("A++", 9, {"mid_max_p": 64, "large_per_p": 1, "large_min": 1024,
+                              "large_max": 4096}),
+             entry("A+-", 5, {"narrow_max_p": 16, "small_max_p": 4}),
+             entry("A--", 2, {"medium_max_p": 0})]
+    srv = tl.Server(64 << 30, max_batch=1, workers=1)
+    srv.set_tuning_table(table)
+    ids = _register(srv, pool)
+    reqs = _requests(pool, 60, 7)
+    res = _run(srv, ids, reqs)
+    for (p, o, a), r in zip(reqs, res):
+        n, e, orders, want = pool[p]
+        assert (r["triangles"], r["hash"]) == want[(o, a)]
+        g = tl.Graph(n, _dev(e))
+        g.order_apply(torch.from_numpy(orders[o]).cuda())
+        _, chosen = autotune.lookup(g.h, a, table)
+        assert r["tuning_entry"] == (table.index(chosen) if chosen else -1), (p, o, a)
+        g.free()
+    srv.set_tuning_table(None)
+    r2 = _run(srv, ids, reqs[:10])
+    assert all(x["tuning_entry"] == -1 for x in r2)
+    srv.close()
