@@ -219,7 +219,13 @@ TL_EXPORT tl_status tl_list_triangles_range(tl_graph *g, tl_alg alg, uint32_t x_
  *           clamp(large_per_p * p, large_min, large_max) tests (large_max is
  *           further capped at 1/16 of the listing's work per large CTA)
  * Every piece rebuilds B, so larger pieces amortise that build; smaller ones
- * balance the end of a launch. */
+ * balance the end of a launch.
+ * narrow_keep_mib and narrow_cold_first set the L2 eviction priority of the
+ * narrow kernel's loads in its short-list steps (four tests per lane spread
+ * over lists shorter than 128 tests): the scanned lists of the highest ranks,
+ * narrow_keep_mib MiB of them (under a degree ordering the most-scanned
+ * lists), are loaded with evict_last, and with narrow_cold_first = 1 the
+ * others with evict_first; 0 and 0 give no hint. */
 typedef struct {
   uint32_t small_max_p;  /* <= 32   (per-warp table of 64 slots) */
   uint32_t medium_max_p; /* <= 1024 (per-warp table of 2048 slots) */
@@ -231,6 +237,8 @@ typedef struct {
   uint32_t large_per_p;  /* >= 1 */
   uint32_t large_min;    /* >= 1024 */
   uint32_t large_max;    /* >= large_min */
+  uint32_t narrow_keep_mib;   /* 0 .. 4096 */
+  uint32_t narrow_cold_first; /* 0 or 1 */
 } tl_tuning;
 /* The defaults (every graph starts with them). */
 TL_EXPORT tl_status tl_default_tuning(tl_tuning *out);

@@ -45,6 +45,8 @@ CANDIDATES = [
     ("narrow_max_p", [256, 128]),
     ("mid_max_p", [2048, 1024]),
     ("medium_max_p", [1024, 256]),
+    ("narrow_keep_mib", [0, 64]),
+    ("narrow_cold_first", [0, 1]),
 ]
 
 

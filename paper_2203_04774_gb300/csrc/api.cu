@@ -74,6 +74,8 @@ tl_tuning tl_default_tuning_value() {
   t.large_per_p = 64;
   t.large_min = 1u << 16;
   t.large_max = 1u << 22;
+  t.narrow_keep_mib = 0;
+  t.narrow_cold_first = 0;
   return t;
 }
 }  // namespace
@@ -192,6 +194,8 @@ tl::Tuning effective_tuning(const tl_tuning &t, uint64_t range_work) {
   tu.mid_piece = t.mid_piece;
   tu.large_per_p = t.large_per_p;
   tu.large_min = t.large_min;
+  tu.narrow_keep_mib = t.narrow_keep_mib;
+  tu.narrow_cold_first = t.narrow_cold_first;
   const uint64_t cap = range_work / (16ull * (uint64_t)tl::tier_grid(tl::kTierLarge));
   uint64_t mx = std::min<uint64_t>(t.large_max, std::max<uint64_t>(cap, t.large_min));
   tu.large_max = (uint32_t)mx;
@@ -384,6 +388,13 @@ tl_status list_impl(tl_graph *G, int alg, uint32_t xb, uint32_t xe, size_t chunk
   a.slabs = G->slabs.as<uint32_t>();
   a.ghash = need_ghash ? G->ghash.as<uint32_t>() : nullptr;
   a.tu = G->used_tu;
+  {
+    // L2 priority of the narrow kernel's short-step loads; the scanned CSR
+    // holds m entries in rank order, so the highest ranks' lists end it
+    const uint64_t keep = (uint64_t)G->tuning.narrow_keep_mib << 18;  // 4-byte entries
+    a.l2_keep_from = keep == 0 ? ~0ull : (g.m > keep ? g.m - keep : 0);
+    a.l2_cold_first = G->tuning.narrow_cold_first;
+  }
 
   if (!G->ev[0]) {
     TL_CUDA(cudaEventCreate(&G->ev[0]));
@@ -738,6 +749,8 @@ tl_status tl_set_tuning(tl_graph *G, const tl_tuning *t) {
     tl::fail(TL_EINVAL, "narrow_piece, mid_piece and large_min must be >= 1024");
   if (v.large_per_p < 1 || v.large_max < v.large_min)
     tl::fail(TL_EINVAL, "large_per_p must be >= 1 and large_max >= large_min");
+  if (v.narrow_keep_mib > 4096 || v.narrow_cold_first > 1)
+    tl::fail(TL_EINVAL, "narrow_keep_mib must be <= 4096 and narrow_cold_first 0 or 1");
   G->tuning = v;
   TL_API_END
 }

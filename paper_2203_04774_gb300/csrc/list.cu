@@ -578,6 +578,27 @@ __device__ void commit_warp(ListCtl *ctl, const ListArgs &a, int64_t t, const ui
   __syncwarp();
 }
 
+// Load of one scanned element in a short-list step.  With kHint (the narrow
+// kernel) it can carry an L2 eviction priority: evict_last for the kept
+// lists (keep), evict_first for the others when cold_first is set; with
+// neither it is a plain load.
+template <bool kHint>
+__device__ __forceinline__ uint32_t load_scanned(const uint32_t *q, bool keep,
+                                                 uint32_t cold_first) {
+  uint32_t v;
+  if (kHint && (keep || cold_first)) {
+    uint64_t pol;
+    if (keep)
+      asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    else
+      asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    asm volatile("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(q), "l"(pol));
+  } else {
+    v = *q;
+  }
+  return v;
+}
+
 // Warp-level walk of the tests [i0, i1) of B vertex x, whose seed row is
 // [pb, pe) (entries of sadj); k0 is the seed edge holding test i0 (found by
 // binary search when ~0).  For each test: z = the scanned element, and
@@ -586,8 +607,9 @@ __device__ void commit_warp(ListCtl *ctl, const ListArgs &a, int64_t t, const ui
 // rank of z) at positions counted by wcnt (kEmit 0, warp tiers), or to the
 // warp's shared-memory buffer as (original id of y, rank of z), flushed to the
 // chunk whenever it could overflow in the next step (kEmit 1, CTA tiers: on a
-// failed flush the walk stops with o.failed set).
-template <int kEmit, bool kPrefetch, class Member, class Verify = NoVerify>
+// failed flush the walk stops with o.failed set).  kHint: the short-list
+// steps' loads take the L2 priorities of a.l2_keep_from / a.l2_cold_first.
+template <int kEmit, bool kPrefetch, bool kHint, class Member, class Verify = NoVerify>
 __device__ __forceinline__ void scan_items(const ListArgs &a, uint64_t pb, uint64_t pe, uint64_t k0,
                                            uint64_t i0, uint64_t i1, uint32_t inv_x,
                                            Member member, uint32_t *slab, WarpOut &o,
@@ -738,7 +760,10 @@ __device__ __forceinline__ void scan_items(const ListArgs &a, uint64_t pb, uint6
       const int jj = j < 31 ? j : 31;
       const uint64_t Aj = shfl_u64(A, jj);
       iyj[u] = __shfl_sync(0xffffffffu, iy, jj);
-      z[u] = act[u] ? a.scan_adj[Aj + base + off] : 0u;
+      const uint64_t q = Aj + base + off;
+      z[u] = act[u] ? load_scanned<kHint>(a.scan_adj + q, kHint && q >= a.l2_keep_from,
+                                          a.l2_cold_first)
+                    : 0u;
     }
     member.check4(z, hit);
     unsigned hm[4];
@@ -809,7 +834,7 @@ __global__ void __launch_bounds__(kWarpThreads, 4) k_list_warp(ListArgs a) {
       __syncwarp();
       for (uint64_t q = pb + lane; q < pe; q += 32) hash_insert(H, lg, a.padj[q]);
       __syncwarp();
-      scan_items<0, false>(a, sb, se, sb, a.WP[sb], a.WP[se], a.inv[x], WarpHashMember{H, lg},
+      scan_items<0, false, false>(a, sb, se, sb, a.WP[sb], a.WP[se], a.inv[x], WarpHashMember{H, lg},
                            slab, nout, cnt, probes);
       __syncwarp();
     }
@@ -949,24 +974,24 @@ __global__ void __launch_bounds__(THREADS, TIER == kTierLarge ? 1 : (TIER == kTi
     if (TIER == kTierNarrow) {
       // the walk tests the filter; staged candidates meet the table at flush
       const SharedBucketVerify vf{sm + kNarrowFilterWords, lg - 2};
-      scan_items<1, kPf>(a, sb, se, ~0ull, wa, wb, inv_x, SmallFilterMember{sm}, nullptr, o,
+      scan_items<1, kPf, kPf>(a, sb, se, ~0ull, wa, wb, inv_x, SmallFilterMember{sm}, nullptr, o,
                          unused, probes, vf);
       if (!o.failed) warp_commit(a, o, inv_x, wb, probes, vf);
     } else if (kLarge && mode == 0) {
-      scan_items<1, kPf>(a, sb, se, ~0ull, wa, wb, inv_x, BitmapMember{sm}, nullptr, o, unused,
+      scan_items<1, kPf, kPf>(a, sb, se, ~0ull, wa, wb, inv_x, BitmapMember{sm}, nullptr, o, unused,
                          probes);
     } else if (!kLarge || mode == 1) {
-      scan_items<1, kPf>(a, sb, se, ~0ull, wa, wb, inv_x, BucketMember{sm, lg - 2}, nullptr, o,
+      scan_items<1, kPf, kPf>(a, sb, se, ~0ull, wa, wb, inv_x, BucketMember{sm, lg - 2}, nullptr, o,
                          unused, probes);
     } else if (mode == 3) {
       // the walk tests the shared filter only; the staged candidates are
       // checked against the CTA's global hash table when the warp flushes
       const GlobalHashVerify vf{a.ghash + (uint64_t)blockIdx.x * kGHashSlots, lg};
-      scan_items<1, kPf>(a, sb, se, ~0ull, wa, wb, inv_x, FilterMember{sm}, nullptr, o, unused,
+      scan_items<1, kPf, kPf>(a, sb, se, ~0ull, wa, wb, inv_x, FilterMember{sm}, nullptr, o, unused,
                          probes, vf);
       if (!o.failed) warp_commit(a, o, inv_x, wb, probes, vf);
     } else {
-      scan_items<1, kPf>(a, sb, se, ~0ull, wa, wb, inv_x,
+      scan_items<1, kPf, kPf>(a, sb, se, ~0ull, wa, wb, inv_x,
                          SortedRowMember{a.padj + pb, pe - pb}, nullptr, o, unused, probes);
     }
     if (!o.failed && TIER != kTierNarrow && (!kLarge || mode != 3))

@@ -45,6 +45,8 @@ struct Tuning {
   uint32_t large_per_p;  // large pieces: clamp(large_per_p * p, large_min, large_max)
   uint32_t large_min;
   uint32_t large_max;
+  uint32_t narrow_keep_mib;   // L2 priority of the narrow kernel's short-step loads
+  uint32_t narrow_cold_first; //   (see l2_keep_from / l2_cold_first in ListArgs)
 };
 __host__ __device__ inline uint64_t piece_work(const Tuning &tu, int tier, uint64_t p) {
   if (tier == kTierNarrow) return tu.narrow_piece;
@@ -131,6 +133,11 @@ struct ListArgs {
   const uint32_t *task_x;
   uint32_t *ghash;               // large tier, n > kBitmapMaxN: kGHashSlots per CTA (or null)
   Tuning tu;                     // the work split the task tables were built with
+  // narrow kernel, short-list steps: loads of scan_adj entries at index >=
+  // l2_keep_from take L2 evict_last, the others evict_first when
+  // l2_cold_first is set (~0 and 0: no hint)
+  uint64_t l2_keep_from;
+  uint32_t l2_cold_first;
   int tier;
   ListCtl *ctl;
   uint32_t *chunk;               // output chunk, 3 uint32 per triangle

@@ -185,6 +185,12 @@ def test_invalid_inputs():
     with pytest.raises(tl.TLError) as ei:
         tl.tl_list_triangles_range(g.h, tl.TL_APP, 2, 1)
     assert ei.value.status == tl.TL_EINVAL
+    for bad in ({"narrow_max_p": 257}, {"warp_work": 255}, {"large_max": 1024},
+                {"narrow_keep_mib": 4097}, {"narrow_cold_first": 2}):
+        with pytest.raises(tl.TLError) as ei:
+            tl.tl_set_tuning(g.h, bad)
+        assert ei.value.status == tl.TL_EINVAL, bad
+        assert tl.tl_get_tuning(g.h) == tl.tl_default_tuning()  # split unchanged
 
 
 def test_many_chunks_k300():
@@ -393,12 +399,16 @@ def test_device_generator_on_gpu_matches_host():
      "large_min": 1 << 16, "large_max": 1 << 26},
     {"small_max_p": 4, "medium_max_p": 40, "narrow_max_p": 16, "mid_max_p": 100},
     {"small_max_p": 0, "medium_max_p": 0, "narrow_max_p": 0, "mid_max_p": 0},
+    # L2 priorities of the narrow kernel's short steps: about half of the
+    # scanned CSR kept (evict_last), the rest evict_first; all kept
+    {"small_max_p": 0, "medium_max_p": 0, "narrow_keep_mib": 1, "narrow_cold_first": 1},
+    {"small_max_p": 0, "medium_max_p": 0, "narrow_keep_mib": 4096},
 ])
 def test_tuning_changes_speed_not_results(tuning):
     """The work split (tl_set_tuning) changes task shapes only: extreme piece
     sizes, warp-task sizes and probe-set thresholds (down to every vertex in
     the large kernel) list the oracle's triangle set with probes = C++ / C+- /
-    C-- (Property 1)."""
+    C-- (Property 1); so do the narrow kernel's L2 load priorities."""
     n = 30000
     e = np.concatenate([synth.chung_lu(n, 30, 2.1, 31), synth.complete(90)])
     rank = synth.order_degree(synth.simple_csr(n, e)[0])
