@@ -232,8 +232,8 @@ void union_of_dags(DeviceGraph &u, uint32_t k, const DeviceGraph *const *parts,
   u.inv.reserve((uint64_t)n * 4);
   u.out_off.reserve(((uint64_t)n + 1) * 8);
   u.in_off.reserve(((uint64_t)n + 1) * 8);
-  u.out_adj.reserve((m + 8) * 4);
-  u.in_adj.reserve((m + 8) * 4);
+  u.out_adj.reserve((m + 4) * 4);
+  u.in_adj.reserve((m + 4) * 4);
   if (m) {
     k_union_keys<<<tiles(m), kThreads, 0, s>>>(
         reinterpret_cast<const uint64_t *const *>(col(0)), m, k, d_eb, d_vb, u.E.as<uint64_t>());

@@ -359,10 +359,10 @@ void build_dag(DeviceGraph &g, const uint32_t *rank, bool on_device) {
 
   g.out_off.reserve(((uint64_t)n + 1) * 8);
   g.in_off.reserve(((uint64_t)n + 1) * 8);
-  // +8 elements: the listing kernels read scanned lists with aligned 16- or
-  // 32-byte loads that may extend up to 7 elements past the last list.
-  g.out_adj.reserve((m + 8) * 4);
-  g.in_adj.reserve((m + 8) * 4);  // scanned by A-- with the same loads
+  // +4 elements: the listing kernels read N+ lists with aligned 16-byte loads
+  // that may extend up to 3 elements past the last list.
+  g.out_adj.reserve((m + 4) * 4);
+  g.in_adj.reserve((m + 4) * 4);  // scanned by A-- with the same 16-byte loads
   if (m > 0) {
     // a3: relabel + orient.
     g.keys_a.reserve(m * 8);
