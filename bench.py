@@ -58,6 +58,12 @@ WORKLOADS = {
                    "avg_degree": 40, "exponent": 2.2, "seed": 4,
                    "ordering": "degree (ties by id), computed on the device",
                    "algorithms": ["A++", "A+-"]},
+    # the same family at n = 8e6 (1.6e8 pairs, a few GB on the device): the
+    # small case for full profiler captures of the listing kernels
+    "chunglu8e6": {"workload": "chunglu8e6-degree", "generator": "Chung-Lu", "n": 8_000_000,
+                   "avg_degree": 40, "exponent": 2.2, "seed": 4,
+                   "ordering": "degree (ties by id), computed on the device",
+                   "algorithms": ["A++", "A+-"]},
     "rmat20": {"workload": "rmat20-degree", "generator": "R-MAT", "scale": 20, "edge_factor": 16,
                "abcd": [0.57, 0.19, 0.19, 0.05], "seed": 2, "ordering": "degree (ties by id)",
                "algorithms": ["A++", "A+-"]},
@@ -70,7 +76,7 @@ DATA = {"Chung-Lu": "synthetic (seeded Chung-Lu power-law graph generated on the
 # k = 0..15, both algorithms, literal form, one thread.  S is chosen per
 # workload for about 1-3 s of CPU work per sample; cpu_baseline repeats the
 # sample, the reference arm times one sample per step.
-ORACLE_SAMPLE_DIV = {"chunglu1e8": 2048, "rmat20": 64}
+ORACLE_SAMPLE_DIV = {"chunglu1e8": 2048, "chunglu8e6": 256, "rmat20": 64}
 
 
 def log(*a):
@@ -886,9 +892,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tl", choices=["tl", "reference"])
     ap.add_argument("--workload", default="all",
-                    choices=["all", "chunglu1e8", "rmat20", "batch4096", "serve"],
+                    choices=["all", "chunglu1e8", "rmat20", "batch4096", "serve", "chunglu8e6"],
                     help="all (default): the 2e9-edge Chung-Lu graph as the headline, with "
-                         "rmat20, batch4096 and serve as sub-objects; or one workload alone")
+                         "rmat20, batch4096 and serve as sub-objects; or one workload alone "
+                         "(chunglu8e6: the headline's family at n = 8e6, for profiler captures)")
     ap.add_argument("--sub-steps", type=int, default=5,
                     help="timed steps of the rmat20 and batch4096 sub-objects")
     ap.add_argument("--serve-requests", type=int, default=0,
@@ -908,7 +915,7 @@ def main():
                               "reference arm; its baseline is the unbatched mode in the same "
                               "line"}))
             return
-        run_reference(args, "rmat20" if wl == "rmat20" else "chunglu1e8")
+        run_reference(args, wl if wl in ("rmat20", "chunglu8e6") else "chunglu1e8")
         return
     world, rank, local = dist_setup()
     worker = None
@@ -934,6 +941,10 @@ def main():
     elif wl == "rmat20":
         line = run_listing(args, "rmat20", args.steps, args.warmup, e2e=not args.no_e2e,
                            orderings=not args.no_orderings,
+                           cpu=None if args.no_cpu or world > 1 else "inline", dist=dist)
+    elif wl == "chunglu8e6":
+        line = run_listing(args, "chunglu8e6", args.steps, args.warmup, e2e=not args.no_e2e,
+                           orderings=False,
                            cpu=None if args.no_cpu or world > 1 else "inline", dist=dist)
     elif wl == "batch4096":
         line = run_batch(args, args.steps, args.warmup)
