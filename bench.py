@@ -658,7 +658,10 @@ def run_batch(args, steps: int, warmup: int) -> dict:
                     "latency_s": {"p50": b_s, "p99": b_s,
                                   "note": "every graph completes when the pass ends"},
                     "list_kernel_ms": sum(st["kernel_ms"]), "list_stats": st,
-                    "work_split": "autotuned for the union's work profile"},
+                    "work_split": "autotuned for the union's work profile",
+                    "launch_mode": "host-driven: one union build and one listing call, the "
+                                   "host launching each kernel and handing full chunks to the "
+                                   "consumer (no CUDA-graph replay)"},
         "batched_fixed_split": {"s_per_step": f_s, "graphs_per_s": k / f_s,
                                 "list_kernel_ms": sum(st2["kernel_ms"]),
                                 "work_split": "library defaults"},
