@@ -224,19 +224,42 @@ def oracle_graph(key: str, threads: int = 1):
     return g, n, time.perf_counter() - t0
 
 
-def oracle_sample(g, n: int, div: int) -> int:
+def oracle_sample(g, n: int, div: int, threads: int = 1) -> int:
     """One sample: both algorithms (literal form) over the sample ranges;
-    returns the triangles listed."""
+    returns the triangles listed.  With threads > 1 the ranges, each cut
+    into eight equal parts, are listed concurrently (the iterations of the
+    outer loop of Algorithms 1 and 2 are independent; the oracle's listing
+    is safe to call from several threads)."""
     import oracle
-    tri = 0
+    tasks = []
     for alg in (oracle.APP, oracle.APM):
         for a, b in sample_ranges(n, div):
-            tri += g.list(alg, oracle.LITERAL, a, b, store=False)[1]
-    return tri
+            if threads == 1:
+                tasks.append((alg, a, b))
+                continue
+            cuts = np.linspace(a, b, 9).astype(np.int64)
+            tasks += [(alg, int(c0), int(c1)) for c0, c1 in zip(cuts[:-1], cuts[1:]) if c1 > c0]
+
+    def one(t):
+        return g.list(t[0], oracle.LITERAL, t[1], t[2], store=False)[1]
+
+    if threads == 1:
+        return sum(one(t) for t in tasks)
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(threads) as ex:
+        return sum(ex.map(one, tasks))
 
 
-def sample_text(key: str, div: int) -> str:
-    return (f"CPU oracle, Algorithms 1 and 2 in the literal boolean-array form, one thread, "
+def oracle_threads(key: str) -> int:
+    """Host threads of the oracle's timed sample: all cores for the 2e9-edge
+    graph (its seed ranges listed concurrently), one for the others (the
+    paper's single-threaded protocol)."""
+    return (os.cpu_count() or 1) if key == "chunglu1e8" else 1
+
+
+def sample_text(key: str, div: int, threads: int = 1) -> str:
+    how = "one thread" if threads == 1 else f"{threads} threads listing parts of the ranges concurrently"
+    return (f"CPU oracle, Algorithms 1 and 2 in the literal boolean-array form, {how}, "
             f"seed ranks [k n/16, k n/16 + n/{16 * div}) for k = 0..15 ({1 / div:.4g} of the "
             f"seed vertices) of the {WORKLOADS[key]['workload']} graph under the same degree "
             f"ordering; listing only (the graph is built first, untimed)")
@@ -244,21 +267,27 @@ def sample_text(key: str, div: int) -> str:
 
 def cpu_baseline_of(g, n: int, key: str, min_s: float = 10.0) -> dict:
     div = ORACLE_SAMPLE_DIV[key]
+    threads = oracle_threads(key)
     tri, reps = 0, 0
     t0 = time.perf_counter()
     while reps == 0 or time.perf_counter() - t0 < min_s:
-        tri += oracle_sample(g, n, div)
+        tri += oracle_sample(g, n, div, threads)
         reps += 1
     dt = time.perf_counter() - t0
-    return {"value": tri / dt, "unit": "triangles/s", "cores": 1, "kind": "oracle",
-            "sample": sample_text(key, div) + f"; {reps} samples, {tri} triangles in {dt:.1f} s"}
+    return {"value": tri / dt, "unit": "triangles/s", "cores": threads, "kind": "oracle",
+            "sample": sample_text(key, div, threads) +
+                      f"; {reps} samples, {tri} triangles in {dt:.1f} s"}
 
 
 def _oracle_worker(conn, key: str, threads: int):
     """Runs in a spawned process: build the oracle's graph of the workload
-    (on the host, while the GPU runs), time the sample, send the result."""
+    (on the host, while the GPU runs); when the parent says the GPU work is
+    done, time the sample and send the result."""
     try:
         g, n, build_s = oracle_graph(key, threads)
+        if not conn.poll(7200):
+            raise TimeoutError("no go-ahead from the bench within 7200 s")
+        conn.recv()
         res = cpu_baseline_of(g, n, key)
         res["build_s"] = round(build_s, 1)
         conn.send(res)
@@ -275,14 +304,17 @@ class OracleWorker:
     def __init__(self, key: str, threads: int = 8):
         import multiprocessing as mp
         ctx = mp.get_context("spawn")
-        self.conn, child = ctx.Pipe(duplex=False)
+        self.conn, child = ctx.Pipe(duplex=True)
         self.proc = ctx.Process(target=_oracle_worker, args=(child, key, threads), daemon=True)
         self.proc.start()
         child.close()
 
     def result(self, timeout_s: float = 1800.0) -> dict:
+        """Called once the GPU work is done: lets the worker time its
+        sample (the host cores are then free) and waits for it."""
         t0 = time.time()
         try:
+            self.conn.send("go")
             if self.conn.poll(timeout_s):
                 res = self.conn.recv()
             else:
@@ -304,10 +336,11 @@ def run_reference(args, key: str):
         return
     g, n, build_s = oracle_graph(key, threads=os.cpu_count() or 1)
     div = ORACLE_SAMPLE_DIV[key]
+    threads = oracle_threads(key)
     for _ in range(args.warmup):
-        oracle_sample(g, n, div)
+        oracle_sample(g, n, div, threads)
     t0 = time.perf_counter()
-    tri = sum(oracle_sample(g, n, div) for _ in range(args.steps))
+    tri = sum(oracle_sample(g, n, div, threads) for _ in range(args.steps))
     dt = time.perf_counter() - t0
     value = tri / dt
     wl = WORKLOADS[key]
@@ -318,8 +351,8 @@ def run_reference(args, key: str):
         "vs_baseline": None, "dtype": "u32", "data": DATA[wl["generator"]],
         "config": dict(wl, n=n, m=g.m, chunk_bytes=CHUNK_BYTES,
                        l2="CPU run (no L2 flush)", oracle_build_s=round(build_s, 1)),
-        "cpu_baseline": {"value": value, "unit": "triangles/s", "cores": 1, "kind": "oracle",
-                         "sample": sample_text(key, div) + "; one sample per step"},
+        "cpu_baseline": {"value": value, "unit": "triangles/s", "cores": threads, "kind": "oracle",
+                         "sample": sample_text(key, div, threads) + "; one sample per step"},
         "e2e": {"value": value, "unit": "triangles/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0}}), flush=True)
 

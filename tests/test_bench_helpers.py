@@ -46,3 +46,17 @@ def test_oracle_sample_ranges():
 def test_h2d_bytes_per_step():
     assert bench.h2d_bytes("chunglu1e8", 100_000_000) == 2_000_000_000 * 8 + 400_000_000
     assert bench.h2d_bytes("rmat20", 1 << 20) == (16 << 20) * 8 + (4 << 20)
+
+
+def test_oracle_sample_threads_split_the_same_work():
+    """The threaded sample lists the same seed ranges as the one-thread one
+    (each range cut into parts), so both count the same triangles."""
+    import oracle
+    from paper_2203_04774_gb300 import synth
+    n = 3000
+    e = synth.chung_lu(n, 12, 2.3, 7)
+    g = oracle.Graph(n, e)
+    g.order_apply(synth.order_degree_from_degrees(g.degrees()))
+    assert bench.oracle_sample(g, n, 4, 1) == bench.oracle_sample(g, n, 4, 5) > 0
+    assert bench.oracle_threads("rmat20") == 1
+    assert bench.oracle_threads("chunglu1e8") == (__import__("os").cpu_count() or 1)
