@@ -225,7 +225,11 @@ TL_EXPORT tl_status tl_list_triangles_range(tl_graph *g, tl_alg alg, uint32_t x_
  * over lists shorter than 128 tests): the scanned lists of the highest ranks,
  * narrow_keep_mib MiB of them (under a degree ordering the most-scanned
  * lists), are loaded with evict_last, and with narrow_cold_first = 1 the
- * others with evict_first; 0 and 0 give no hint. */
+ * others with evict_first; 0 and 0 give no hint.
+ * large_hash_max_p: on graphs of more than 2^20 ranks, a large vertex with
+ * p <= large_hash_max_p is probed in a shared-memory bucketed hash table, a
+ * larger one through a shared-memory filter whose candidates are checked
+ * against the CTA's hash table in global memory when its warp flushes. */
 typedef struct {
   uint32_t small_max_p;  /* <= 32   (per-warp table of 64 slots) */
   uint32_t medium_max_p; /* <= 1024 (per-warp table of 2048 slots) */
@@ -239,6 +243,7 @@ typedef struct {
   uint32_t large_max;    /* >= large_min */
   uint32_t narrow_keep_mib;   /* 0 .. 4096 */
   uint32_t narrow_cold_first; /* 0 or 1 */
+  uint32_t large_hash_max_p;  /* <= 16384 (per-CTA table of 32768 slots) */
 } tl_tuning;
 /* The defaults (every graph starts with them). */
 TL_EXPORT tl_status tl_default_tuning(tl_tuning *out);

@@ -74,7 +74,8 @@ class Tuning(ctypes.Structure):
                 ("mid_max_p", _U32), ("warp_work", _U32), ("narrow_piece", _U32),
                 ("mid_piece", _U32),
                 ("large_per_p", _U32), ("large_min", _U32), ("large_max", _U32),
-                ("narrow_keep_mib", _U32), ("narrow_cold_first", _U32)]
+                ("narrow_keep_mib", _U32), ("narrow_cold_first", _U32),
+                ("large_hash_max_p", _U32)]
 
     def as_dict(self) -> dict:
         return {name: int(getattr(self, name)) for name, _ in self._fields_}

@@ -47,6 +47,7 @@ CANDIDATES = [
     ("medium_max_p", [1024, 256]),
     ("narrow_keep_mib", [0, 64]),
     ("narrow_cold_first", [0, 1]),
+    ("large_hash_max_p", [16384, 0]),
 ]
 
 

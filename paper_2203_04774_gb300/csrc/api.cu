@@ -76,6 +76,7 @@ tl_tuning tl_default_tuning_value() {
   t.large_max = 1u << 22;
   t.narrow_keep_mib = 0;
   t.narrow_cold_first = 0;
+  t.large_hash_max_p = tl::kHashMaxSlots / 2;
   return t;
 }
 }  // namespace
@@ -196,6 +197,7 @@ tl::Tuning effective_tuning(const tl_tuning &t, uint64_t range_work) {
   tu.large_min = t.large_min;
   tu.narrow_keep_mib = t.narrow_keep_mib;
   tu.narrow_cold_first = t.narrow_cold_first;
+  tu.large_hash_max_p = t.large_hash_max_p;
   const uint64_t cap = range_work / (16ull * (uint64_t)tl::tier_grid(tl::kTierLarge));
   uint64_t mx = std::min<uint64_t>(t.large_max, std::max<uint64_t>(cap, t.large_min));
   tu.large_max = (uint32_t)mx;
@@ -207,7 +209,8 @@ bool same_tuning(const tl::Tuning &a, const tl::Tuning &b) {
          a.narrow_max_p == b.narrow_max_p && a.mid_max_p == b.mid_max_p &&
          a.warp_work == b.warp_work && a.narrow_piece == b.narrow_piece &&
          a.mid_piece == b.mid_piece && a.large_per_p == b.large_per_p &&
-         a.large_min == b.large_min && a.large_max == b.large_max;
+         a.large_min == b.large_min && a.large_max == b.large_max &&
+         a.large_hash_max_p == b.large_hash_max_p;
 }
 
 // WP, the exclusive prefix of the scanned-list lengths over all seed-side
@@ -751,6 +754,8 @@ tl_status tl_set_tuning(tl_graph *G, const tl_tuning *t) {
     tl::fail(TL_EINVAL, "large_per_p must be >= 1 and large_max >= large_min");
   if (v.narrow_keep_mib > 4096 || v.narrow_cold_first > 1)
     tl::fail(TL_EINVAL, "narrow_keep_mib must be <= 4096 and narrow_cold_first 0 or 1");
+  if (v.large_hash_max_p > tl::kHashMaxSlots / 2)
+    tl::fail(TL_EINVAL, "large_hash_max_p must be <= 16384");
   G->tuning = v;
   TL_API_END
 }

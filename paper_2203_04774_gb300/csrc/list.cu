@@ -308,6 +308,7 @@ struct WarpOut {
 // function of its own so that the walk keeps its registers.
 struct NoVerify {
   static constexpr bool kActive = false;
+  __device__ void prefetch(uint32_t) const {}
 };
 
 __device__ __noinline__ uint32_t verify_bucket(uint32_t *buf, uint32_t cnt, const uint32_t *H,
@@ -337,6 +338,7 @@ struct SharedBucketVerify {
   static constexpr bool kActive = true, kOutOfLine = true;
   const uint32_t *H;
   int lgb;
+  __device__ void prefetch(uint32_t) const {}
   __device__ uint32_t run(uint32_t *buf, uint32_t cnt) const {
     return verify_bucket(buf, cnt, H, lgb);
   }
@@ -346,6 +348,11 @@ struct GlobalHashVerify {
   static constexpr bool kActive = true, kOutOfLine = false;
   const uint32_t *H;
   int lg;
+  // a candidate's first slot is asked into L2 when the candidate is staged,
+  // so that the check at flush finds it there
+  __device__ void prefetch(uint32_t z) const {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(H + hslot(z, lg)));
+  }
   __device__ void check4(const uint32_t z[4], const bool valid[4], bool res[4]) const {
     const uint32_t mask = (1u << lg) - 1u;
     uint32_t h[4];
@@ -721,6 +728,7 @@ __device__ __forceinline__ void scan_items(const ListArgs &a, uint64_t pb, uint6
               slab[3 * r + 2] = z[u];
             } else {
               reinterpret_cast<uint2 *>(o.buf)[r] = make_uint2(iyj, z[u]);
+              vf.prefetch(z[u]);
             }
           }
         }
@@ -796,6 +804,7 @@ __device__ __forceinline__ void scan_items(const ListArgs &a, uint64_t pb, uint6
             slab[3 * r + 2] = z[u];
           } else {
             reinterpret_cast<uint2 *>(o.buf)[r] = make_uint2(iyj[u], z[u]);
+            vf.prefetch(z[u]);
           }
         }
       }
@@ -905,7 +914,8 @@ __global__ void __launch_bounds__(THREADS, TIER == kTierLarge ? 1 : (TIER == kTi
     while ((1ull << lg) < want && (1u << lg) < max_slots) ++lg;
     s_lg = lg;
     s_mode = (2 * p <= (1ull << lg)) ? 1 : 2;  // 2: too large, binary search
-    if (TIER == kTierLarge && s_mode == 2 && a.ghash && 2 * p <= kGHashSlots) {
+    if (TIER == kTierLarge && (s_mode == 2 || p > a.tu.large_hash_max_p) && a.ghash &&
+        2 * p <= kGHashSlots) {
       // 3: shared-memory filter + this CTA's hash table in global memory
       lg = 6;
       while ((1ull << lg) < 2 * p) ++lg;

@@ -47,6 +47,7 @@ struct Tuning {
   uint32_t large_max;
   uint32_t narrow_keep_mib;   // L2 priority of the narrow kernel's short-step loads
   uint32_t narrow_cold_first; //   (see l2_keep_from / l2_cold_first in ListArgs)
+  uint32_t large_hash_max_p;  // n > kBitmapMaxN: larger large vertices take filter + global table
 };
 __host__ __device__ inline uint64_t piece_work(const Tuning &tu, int tier, uint64_t p) {
   if (tier == kTierNarrow) return tu.narrow_piece;

@@ -91,7 +91,7 @@ def test_tuning_defaults_and_argument_checks_without_gpu(built):
                  "mid_max_p": 2048, "warp_work": 4096, "narrow_piece": 1 << 14,
                  "mid_piece": 1 << 16,
                  "large_per_p": 64, "large_min": 1 << 16, "large_max": 1 << 22,
-                 "narrow_keep_mib": 0, "narrow_cold_first": 0}
+                 "narrow_keep_mib": 0, "narrow_cold_first": 0, "large_hash_max_p": 16384}
     assert built.tl_set_tuning(None, None) == tl.TL_EINVAL
     out = tl.Tuning()
     assert built.tl_get_tuning(None, ctypes.byref(out)) == tl.TL_EINVAL

@@ -186,7 +186,7 @@ def test_invalid_inputs():
         tl.tl_list_triangles_range(g.h, tl.TL_APP, 2, 1)
     assert ei.value.status == tl.TL_EINVAL
     for bad in ({"narrow_max_p": 257}, {"warp_work": 255}, {"large_max": 1024},
-                {"narrow_keep_mib": 4097}, {"narrow_cold_first": 2}):
+                {"narrow_keep_mib": 4097}, {"narrow_cold_first": 2}, {"large_hash_max_p": 16385}):
         with pytest.raises(tl.TLError) as ei:
             tl.tl_set_tuning(g.h, bad)
         assert ei.value.status == tl.TL_EINVAL, bad
@@ -295,10 +295,12 @@ def test_every_tier_runs_and_matches():
     assert np.all(seen > 0), seen
 
 
-def test_large_n_hash_probe_path():
+@pytest.mark.parametrize("large_hash_max_p", [16384, 0])
+def test_large_n_hash_probe_path(large_hash_max_p):
     """n above the shared-memory bitmap limit (1,572,864 ranks): the large
     kernel probes with a shared-memory hash table, and with binary search for
-    probe sets too large for it (a star-like hub with 40,000 neighbours)."""
+    probe sets too large for it (a star-like hub with 40,000 neighbours); with
+    large_hash_max_p = 0 every large vertex takes the filter + global table."""
     n = 2_000_000
     e1 = synth.chung_lu(n, 4, 2.1, 12)
     hub = np.stack([np.zeros(40000, np.uint32), np.arange(1, 40001, dtype=np.uint32)], 1)
@@ -313,6 +315,7 @@ def test_large_n_hash_probe_path():
     orders = [("degree", synth.order_degree(off)), ("identity", synth.order_identity(n)),
               ("reverse", (n - 1 - np.arange(n)).astype(np.uint32))]
     g = tl.Graph(n, _dev(e))
+    tl.tl_set_tuning(g.h, {"large_hash_max_p": large_hash_max_p})
     ref = oracle.Graph(n, e)
     for name, rank in orders:
         g.order_apply(_dev(rank))
@@ -403,6 +406,7 @@ def test_device_generator_on_gpu_matches_host():
     # scanned CSR kept (evict_last), the rest evict_first; all kept
     {"small_max_p": 0, "medium_max_p": 0, "narrow_keep_mib": 1, "narrow_cold_first": 1},
     {"small_max_p": 0, "medium_max_p": 0, "narrow_keep_mib": 4096},
+    {"mid_max_p": 300, "large_hash_max_p": 0},
 ])
 def test_tuning_changes_speed_not_results(tuning):
     """The work split (tl_set_tuning) changes task shapes only: extreme piece
